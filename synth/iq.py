@@ -1,0 +1,116 @@
+"""Analytic baseband IQ channel data for plane-wave acquisitions (forward model).
+
+Physical model (the readings the beamformer is checked against):
+  * a plane wave with direction u = (sin az cos el, sin el, cos az cos el) passes the
+    array origin at t = 0, so it reaches point p at (u . p) / c;
+  * a point scatterer of amplitude A at p re-emits a spherical wave, reaching element
+    e at |p - e| / c later: round-trip time tau = (u . p + |p - e|) / c;
+  * the received RF echo is A g(t - tau) cos(2 pi fc (t - tau)) with a Gaussian
+    envelope g of full width at half maximum 2 / fc (a 2-cycle pulse);
+  * IQ demodulation (multiply by exp(-j 2 pi fc t), low-pass) leaves
+    IQ(t) = (A / 2) g(t - tau) exp(-j 2 pi fc tau), sampled at t_n = t0 + n / fs;
+  * no spreading loss and no element directivity.
+
+The envelope is truncated to the 2K taps around tau (|n - s_tau| < K, K = ceil(4 sigma)).
+Synthesis runs in torch on any device; its precision does not matter to the parity
+tests because the oracle and the GPU library are fed the same stored array.
+"""
+from __future__ import annotations
+
+import math
+from typing import Optional
+
+import numpy as np
+import torch
+
+from .acquisition import Acquisition, pulse_sigma_samples
+from .phantoms import Phantom
+
+
+def plane_wave_directions(acq: Acquisition) -> np.ndarray:
+    az, el = acq.tx_angles[:, 0], acq.tx_angles[:, 1]
+    return np.stack([np.sin(az) * np.cos(el), np.sin(el), np.cos(az) * np.cos(el)], axis=1)
+
+
+def envelope_taps(acq: Acquisition) -> int:
+    return int(math.ceil(4.0 * pulse_sigma_samples(acq)))
+
+
+def add_echoes(buf: torch.Tensor, acq: Acquisition, pos: np.ndarray, amp: np.ndarray,
+               chunk_elems: int = 1 << 24) -> None:
+    """Add the echoes of scatterers (pos [J,3], real amp [J]) into ``buf``
+    (complex [T, C, S], any device), in place."""
+    if len(pos) == 0:
+        return
+    dev = buf.device
+    fdt = torch.float64 if buf.dtype == torch.complex128 else torch.float32
+    T, C, S = buf.shape
+    u = torch.as_tensor(plane_wave_directions(acq), dtype=fdt, device=dev)       # [T,3]
+    el = torch.as_tensor(acq.elem_pos.astype(np.float64), dtype=fdt, device=dev)  # [C,3]
+    K = envelope_taps(acq)
+    sig = pulse_sigma_samples(acq)
+    offs = torch.arange(-K + 1, K + 1, device=dev, dtype=torch.int64)           # [2K]
+    flat = torch.view_as_real(buf).reshape(-1, 2)
+    per = max(1, chunk_elems // (T * C * 2 * K))
+    base_tc = (torch.arange(T, device=dev)[:, None] * C + torch.arange(C, device=dev)[None, :]) * S
+    for j0 in range(0, len(pos), per):
+        p = torch.as_tensor(pos[j0:j0 + per], dtype=fdt, device=dev)            # [J,3]
+        a = torch.as_tensor(amp[j0:j0 + per], dtype=fdt, device=dev)            # [J]
+        tau_tx = (u @ p.T) / acq.c                                               # [T,J]
+        tau_rx = torch.linalg.norm(p[None, :, :] - el[:, None, :], dim=-1) / acq.c  # [C,J]
+        tau = tau_tx[:, None, :] + tau_rx[None, :, :]                            # [T,C,J]
+        s = (tau - acq.t0) * acq.fs
+        n = torch.floor(s).to(torch.int64)[..., None] + offs                     # [T,C,J,2K]
+        g = torch.exp(-((n.to(fdt) - s[..., None]) ** 2) / (2.0 * sig * sig))
+        ph = -2.0 * math.pi * acq.fc * tau
+        mag = 0.5 * a[None, None, :, None] * g
+        vre = mag * torch.cos(ph)[..., None]
+        vim = mag * torch.sin(ph)[..., None]
+        ok = (n >= 0) & (n < S)
+        idx = (base_tc[:, :, None, None] + n)[ok]
+        flat.index_add_(0, idx, torch.stack([vre[ok], vim[ok]], dim=-1))
+
+
+def simulate(acq: Acquisition, phantom: Phantom, seed: int = 0, snr_db: Optional[float] = None,
+             device="cpu", accum=torch.complex128, static_frames: bool = False) -> torch.Tensor:
+    """IQ tensor complex64 [T, C, S, F] (frames contiguous) for ``phantom``.
+
+    ``snr_db``: if given, complex Gaussian noise of power 10^(-snr/10) * mean |IQ|^2
+    (noise-free data, frame 0) is added independently to every frame, from a torch
+    generator seeded with ``seed``.  ``static_frames``: the moving part is ignored and
+    every frame is the static echo plus its own noise.
+    """
+    T, C, S, F = acq.iq_shape
+    dev = torch.device(device)
+    stat = torch.zeros((T, C, S), dtype=accum, device=dev)
+    add_echoes(stat, acq, phantom.static_pos, phantom.static_amp)
+    out = torch.empty((T, C, S, F), dtype=torch.complex64, device=dev)
+    ref_power = None
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed) * 1000003 + 17)
+    for f in range(F):
+        if phantom.moving is not None and not static_frames:
+            fr = stat.clone()
+            mp, ma = phantom.moving(f)
+            add_echoes(fr, acq, mp, ma)
+        else:
+            fr = stat
+        if snr_db is not None:
+            if ref_power is None:
+                ref_power = float((fr.abs() ** 2).mean())
+            sd = math.sqrt(ref_power * 10.0 ** (-snr_db / 10.0) / 2.0)
+            noise = torch.randn((T, C, S, 2), generator=gen, device=dev, dtype=torch.float32) * sd
+            out[..., f] = fr.to(torch.complex64) + torch.view_as_complex(noise)
+        else:
+            out[..., f] = fr.to(torch.complex64)
+    return out
+
+
+def to_f16x2(iq: torch.Tensor) -> torch.Tensor:
+    """complex64 [T,C,S,F] -> float16 [T,C,S,F,2] (re, im interleaved), round to nearest."""
+    return torch.view_as_real(iq).to(torch.float16).contiguous()
+
+
+def from_f16x2(iq16: torch.Tensor) -> torch.Tensor:
+    """float16 [...,2] -> complex64 (exact widening)."""
+    return torch.view_as_complex(iq16.to(torch.float32).contiguous())
