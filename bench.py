@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark: ensemble Power Doppler delay-and-sum, points per second (Eq. 1).
+
+Workload: the rotating-disk Doppler benchmark shape of Sec. 4.1 as a seeded synthetic
+stand-in -- 256 x 256 pixels at 0.1 mm, 128-element linear array, one 0-degree plane
+wave, 32 frames, 2048 complex64 samples per channel, F# 1.0 -- writing both the complex
+frames (B-mode) and Power Doppler.  One step = one mach_power_doppler call on IQ already
+resident in HBM; L2 is flushed (256 MB write) between steps, outside the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: each rank beamforms its own acquisition (weak scaling, no
+data-path collective); the time is the maximum over ranks.  ``--impl reference`` times
+the FP64 CPU oracle on the same workload instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DAS points/s (voxel x channel x transmit x frame, Eq. 1)"
+UNIT = "points/s"
+PAPER_POINTS_PER_S = 258_052_096 / 0.23e-3      # Sec. 4.2: 0.23 ms on an RTX 5090, 251^2 px
+KERNEL_SOURCES = ("k_das.cu", "das_term.cuh", "mach_internal.h")
+FLUSH_BYTES = 256 << 20                           # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="doppler2d")
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers ----
+
+def dist_init(n):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and not dist.is_initialized():
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2604_06257_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(variant: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        data = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    e = data.get(f"{variant}@{workload}")
+    if not e or e.get("kernel_sha") != kernel_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """Samples nvidia-smi every 200 ms while running."""
+    Q = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, uuid: str):
+        self.uuid = uuid.replace("GPU-", "").lower()
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        rows = []
+        for line in open(self.out.name):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9 or not parts[0].lower().endswith(self.uuid[-12:]):
+                continue
+            rows.append(parts)
+        os.unlink(self.out.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "", 1).isdigit()]
+        reasons = sorted({n for r in rows for n, v in zip(self.NAMES, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_median": statistics.median(pw) if pw else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def workload_config(acq, extra=None):
+    d = {"workload": f"{acq.name}: rotating-disk Doppler stand-in (Sec. 4.1 shape), "
+                     f"{acq.grid_dims[0]}x{acq.grid_dims[2]} px, {acq.n_elem} ch, {acq.n_tx} tx, "
+                     f"{acq.n_frames} frames, {acq.n_samples} samples, {acq.iq_dtype} IQ, "
+                     f"F# {acq.f_number} {acq.apod}; outputs B-mode frames + Power Doppler",
+         "voxels": acq.n_vox, "channels": acq.n_elem, "transmits": acq.n_tx,
+         "frames": acq.n_frames, "samples": acq.n_samples,
+         "points_per_step": acq.points,
+         "l2": "flushed between timed steps (256 MB write, outside the timed events)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def oracle_sample(acq, iq_host, seconds, min_vox=64):
+    """Time the oracle on an evenly strided voxel sample sized to ~``seconds``."""
+    import numpy as np
+    import oracle
+    cal = np.arange(0, acq.n_vox, max(1, acq.n_vox // 512))[:512]
+    t = time.perf_counter()
+    oracle.das(acq, iq_host, cal, want_y=False)
+    dt = max(time.perf_counter() - t, 1e-6)
+    n = int(min(acq.n_vox, max(min_vox, len(cal) * seconds / dt)))
+    idx = np.linspace(0, acq.n_vox - 1, n).astype(np.int64)
+    t = time.perf_counter()
+    oracle.das(acq, iq_host, idx, want_y=False)
+    dt = time.perf_counter() - t
+    pts = n * acq.n_elem * acq.n_tx * acq.n_frames
+    return {"value": pts / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{n} of {acq.n_vox} voxels (evenly strided), all channels, transmits "
+                      f"and frames; one call, {dt:.2f} s, FP64"}
+
+
+# ---------------------------------------------------------------- our arm ----
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import synth
+    import paper_2604_06257_gb300 as m
+    from paper_2604_06257_gb300 import build as pkg_build, counts, shard
+
+    rank, world, local = dist_init(args.gpus)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    pkg_build.build()
+    m.lib()
+
+    acq, iq = synth.make(args.workload, "full", device=dev, seed=synth.SEEDS[args.workload] + rank)
+    plan = m.Plan(**m.plan_kwargs(acq))
+    info = plan.info()
+    V, F = acq.n_vox, acq.n_frames
+    pd = torch.empty(V, dtype=torch.float32, device=dev)
+    y = torch.empty((V, F), dtype=torch.complex64, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    i0, _, _ = plan.terms(np.arange(V))
+    active_terms = int((i0 >= 0).sum().item())
+    active_points = active_terms * F
+    launches_per_step = 1 + (1 if info["frame_tiles"] > 1 else 0)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        m.mach_power_doppler(plan.handle, iq, pd, y)
+    torch.cuda.synchronize()
+    barrier()
+
+    props = torch.cuda.get_device_properties(dev)
+    clocks = Clocks(str(getattr(props, "uuid", "")))
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        m.mach_power_doppler(plan.handle, iq, pd, y)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    times_ms = [a.elapsed_time(b) for a, b in ev]
+    t_sum = sum(times_ms) / 1e3
+    t_max = shard.max_over_ranks(t_sum)
+    value = world * acq.points * args.steps / t_max
+    t_launch = statistics.mean(times_ms) / 1e3
+
+    # roofline: the gather-MAC is bound by the SM load path and the FP32 pipe, not HBM.
+    n_sm = props.multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12                     # TFLOP/s
+    flops = active_points * 16.0                                            # 8 FMA per term-frame
+    achieved = flops / t_launch / 1e12
+    comp = counts.compulsory_bytes(V, acq.n_elem, acq.n_tx, acq.n_samples, F, write_y=True, write_pd=True)
+    traffic = profiled_traffic(info["variant"], acq.name)
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": traffic,
+            "kernel": info["variant"],
+            "peak_source": f"FP32 FMA: {n_sm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz "
+                           "(max SM clock, MEASURED_PEAKS.json)",
+            "algorithmic": "16 flop (8 FP32 FMA) per active term-frame; active = in aperture "
+                           f"and in range: {active_terms} of {V * acq.n_elem * acq.n_tx} terms",
+            "hbm": {"compulsory_bytes": comp, "achieved_gbs": comp / t_launch / 1e9,
+                    "peak_gbs": hbm_peak, "frac": comp / t_launch / 1e9 / hbm_peak},
+            "sm_load_path": {"bytes_per_term_frame": 16,
+                             "achieved_gbs": active_points * 16 / t_launch / 1e9}}
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    e2e = None
+    if args.e2e_steps > 0:
+        iq_pin = iq.cpu().pin_memory()
+        pd_pin = torch.empty(V, dtype=torch.float32).pin_memory()
+        y_pin = torch.empty((V, F), dtype=torch.complex64).pin_memory()
+        for _ in range(3):
+            plan.power_doppler_host(iq_pin, pd_pin, y_pin)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            plan.power_doppler_host(iq_pin, pd_pin, y_pin)
+        te = shard.max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": world * acq.points * args.e2e_steps / te, "unit": UNIT,
+               "h2d_bytes_per_step": iq_pin.numel() * iq_pin.element_size(),
+               "d2h_bytes_per_step": pd_pin.numel() * 4 + y_pin.numel() * 8,
+               "steps": args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(acq, iq.cpu(), args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": workload_config(acq, {"parallelism": f"replicas{world}",
+                                                "kernel_variant": info["variant"],
+                                                "active_fraction": active_terms / (V * acq.n_elem * acq.n_tx)}),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches_per_step * args.steps,
+                "clocks": clk, "wall_s_timed_region": t_wall,
+                "paper_context": {"points_per_s": PAPER_POINTS_PER_S,
+                                  "what": "Sec. 4.2: 0.23 ms on an RTX 5090 for the 251x251 px "
+                                          "PyMUST rotating-disk dataset (not this exact workload)",
+                                  "ratio": value / PAPER_POINTS_PER_S}}
+        print(json.dumps(line))
+    plan.close()
+
+
+# ---------------------------------------------------------- reference arm ----
+
+def run_reference(args):
+    import numpy as np
+    import torch
+    import synth
+    import oracle
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    if torch.cuda.is_available():
+        acq, iq = synth.make(args.workload, "full", device="cuda")
+        iq_host = iq.cpu()
+        del iq
+        src = "seeded synthetic IQ (generated on the GPU, copied to host)"
+    else:
+        acq = synth.make_acquisition(args.workload, "full")
+        iq_host = synth.random_iq(acq, 0)
+        src = "seeded complex Gaussian IQ (no GPU to synthesise the phantom)"
+    budget = 120.0                                     # whole run within about two minutes
+    per_step = min(20.0, max(0.02, budget / max(1, args.steps + args.warmup)))
+    cal = np.arange(0, acq.n_vox, max(1, acq.n_vox // 256))[:256]
+    t = time.perf_counter()
+    oracle.das(acq, iq_host, cal, want_y=False)
+    dt = max(time.perf_counter() - t, 1e-6)
+    n = int(min(acq.n_vox, max(16, len(cal) * per_step / dt)))
+    idx = np.linspace(0, acq.n_vox - 1, n).astype(np.int64)
+    for _ in range(args.warmup):
+        oracle.das(acq, iq_host, idx, want_y=True)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.das(acq, iq_host, idx, want_y=True)
+        times.append(time.perf_counter() - t)
+    pts = n * acq.n_elem * acq.n_tx * acq.n_frames
+    value = pts / statistics.mean(times)
+    cores = oracle.max_threads()
+    sample = (f"{n} of {acq.n_vox} voxels (evenly strided) per step, all channels, transmits and "
+              f"frames, FP64, {src}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.mean(times) * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(acq, {"parallelism": "host cores (OpenMP)"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+    try:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+    except Exception:
+        pass
+
+
+if __name__ == "__main__":
+    main()

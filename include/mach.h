@@ -1,0 +1,168 @@
+/*
+ * mach.h -- C ABI of the GB300 delay-and-sum (DAS) beamforming library.
+ *
+ * Method: delay-and-sum of baseband IQ channel data from plane-wave acquisitions
+ * (arXiv 2604.06257, Sec. 2.1): for every voxel, compute the round-trip delay to each
+ * receiving element, interpolate the received signal at that delay, and sum coherently
+ * over elements and compounded transmits; Power Doppler sums |.|^2 over the frame
+ * ensemble (Sec. 5).  Transmit arrival times are precomputed once per plan and receive
+ * delays are computed on the fly (hybrid delays, Sec. 4.3).  Work is counted with Eq. 1:
+ * voxels x channels x transmits x frames.
+ *
+ * Conventions (all entry points):
+ *  - Units: metres, seconds, hertz, radians.  Axes x lateral, y elevation, z depth; the
+ *    array lies in z = 0 for the aperture rule.
+ *  - IQ layout in device memory: [n_tx][n_elem][n_samples][n_frames], frames contiguous
+ *    (Sec. 4.4 stores [elements, samples, frames]; this ABI adds the transmit axis in
+ *    front).  Element type: MACH_IQ_C64 = interleaved float32 (re, im) ("complex64",
+ *    Sec. 4.1); MACH_IQ_F16X2 = interleaved float16 (re, im), widened to float32 before
+ *    any arithmetic.
+ *  - Output layout: y complex64 [n_vox][n_frames] (frames contiguous); Power Doppler
+ *    float32 [n_vox].  Voxel order = the order of vox_pos, or for a regular grid
+ *    v = ix + nx*(iy + ny*iz).
+ *  - Ownership: the caller owns every IQ and output buffer.  A plan copies every host
+ *    array it is given at creation and owns its device tables; it never keeps a caller
+ *    pointer.
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Run calls
+ *    are stream-ordered and asynchronous; they never synchronise the host.
+ *  - Errors: arguments are checked before anything is launched; a call that returns an
+ *    error before launching leaves the outputs untouched.  CUDA errors map to
+ *    MACH_ERR_CUDA.  No C++ exception crosses this boundary.
+ *  - Threads: a plan is read-only after creation.  Calls that share a plan may run on
+ *    different streams concurrently, except when mach_plan_info.frame_tiles > 1 and
+ *    Power Doppler is requested (those calls share the plan's partial-sum scratch and
+ *    must be ordered on one stream).
+ */
+#ifndef MACH_H
+#define MACH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MACH_OK = 0,
+    MACH_ERR_INVALID_ARG = 1,   /* a NULL pointer, a size out of range, inconsistent geometry */
+    MACH_ERR_CUDA = 2,          /* a CUDA runtime call or a launch failed                     */
+    MACH_ERR_OOM = 3,           /* device allocation failed, or the plan would not fit        */
+    MACH_ERR_UNSUPPORTED = 4,   /* valid request outside what this build implements          */
+    MACH_ERR_TIMEOUT = 5        /* a bounded device-side wait gave up                         */
+} mach_status;
+
+/* F-number aperture windows (Sec. 4.1 "f-number").  With rho the lateral distance
+ * voxel-element and dz the depth difference, an element contributes iff dz > 0 and
+ * rho * 2 * f_number <= dz.  Window of t = rho * f_number / dz in [0, 1/2]:
+ * BOXCAR 1, HANN cos^2(pi t), GAUSS exp(-8 t^2).  NONE: every element, weight 1. */
+typedef enum {
+    MACH_APOD_NONE = 0,
+    MACH_APOD_BOXCAR = 1,
+    MACH_APOD_HANN = 2,
+    MACH_APOD_GAUSS = 3
+} mach_apod;
+
+typedef enum {
+    MACH_IQ_C64 = 0,     /* float32 (re, im) per sample, 8 bytes */
+    MACH_IQ_F16X2 = 1    /* float16 (re, im) per sample, 4 bytes */
+} mach_iq_dtype;
+
+typedef struct mach_plan_s *mach_plan;
+
+/* Everything a plan needs (the inputs of Sec. 3.3's workflow and Table 3). */
+typedef struct {
+    int32_t ndim;                /* 2 (all y = 0, elevation angles 0) or 3               */
+    int32_t n_elem;              /* receiving elements (channels), >= 1                  */
+    const float *elem_pos;       /* host [n_elem][3] element positions, metres           */
+    int64_t n_vox;               /* voxels: size of vox_pos, or 0 / nx*ny*nz for a grid  */
+    const float *vox_pos;        /* host [n_vox][3] voxel positions, or NULL -> grid     */
+    int32_t grid_dims[3];        /* regular grid (nx, ny, nz), x fastest                 */
+    double grid_origin[3];       /* position of voxel (0, 0, 0), metres                  */
+    double grid_step[3];         /* spacing per axis, metres                             */
+    int32_t n_tx;                /* transmits compounded coherently, >= 1                */
+    const double *tx_angles;     /* host [n_tx][2] plane-wave (azimuth, elevation), rad;
+                                    direction u = (sin az cos el, sin el, cos az cos el),
+                                    wavefront at the array origin at t = 0               */
+    const float *tx_table_dev;   /* optional DEVICE [n_tx][n_vox] transmit arrival times
+                                    in seconds (e.g. from a simulator, Sec. 3.3/4.3);
+                                    when set it replaces the plane-wave model and
+                                    tx_angles may be NULL.  Read during mach_das_plan only */
+    double fs;                   /* IQ sampling rate, Hz, > 0                            */
+    double fc;                   /* demodulation (centre) frequency, Hz, >= 0            */
+    double c;                    /* speed of sound, m/s, > 0                             */
+    double t0;                   /* time of sample 0, s                                  */
+    double f_number;             /* >= 0                                                  */
+    int32_t apod;                /* mach_apod                                            */
+    int32_t n_samples;           /* samples per channel, 2 .. 2^24                       */
+    int32_t n_frames;            /* frames (ensemble), >= 1                              */
+    int32_t iq_dtype;            /* mach_iq_dtype                                        */
+} mach_das_desc;
+
+/* Build a plan (Sec. 4.3 precompute): validates `d`, copies its host arrays, allocates
+ * the device tables (voxel coordinates in sample units, element coordinates, the
+ * transmit delay table [n_tx][n_vox] float32 built in FP64 on the device) and selects
+ * the kernel variant.  Runs on `stream` and synchronises it before returning.
+ * Errors: INVALID_ARG (checked before any CUDA call), OOM, CUDA, UNSUPPORTED.
+ * On error *out is set to NULL and nothing is leaked. */
+mach_status mach_das_plan(const mach_das_desc *d, void *stream, mach_plan *out);
+
+/* Delay-and-sum (Sec. 2.1 steps 1-3, compounding over all transmits):
+ *   y[v][f] = sum_t sum_c a(v,c) e^{+j 2 pi fc (t0 + s/fs)} lerp(iq[t][c][.][f], s)
+ * with s = s_tx(t,v) + |p_v - e_c| fs / c, linear interpolation between samples
+ * floor(s) and floor(s)+1, and a term dropped unless 0 <= s < n_samples - 1.
+ * iq_dev: device IQ as described above.  y_dev: device complex64 [n_vox][n_frames].
+ * Errors: INVALID_ARG (NULL plan or pointer), CUDA. */
+mach_status mach_das_run(mach_plan p, const void *iq_dev, void *y_dev, void *stream);
+
+/* Ensemble Power Doppler (Sec. 5): pd[v] = sum_f |y[v][f]|^2, fused into the same
+ * kernel as the DAS sums; y_dev_or_null additionally receives the complex frames
+ * (B-mode data) when not NULL.  pd_dev: device float32 [n_vox].
+ * Errors: INVALID_ARG, CUDA. */
+mach_status mach_power_doppler(mach_plan p, const void *iq_dev, float *pd_dev,
+                               void *y_dev_or_null, void *stream);
+
+/* Release a plan and its device tables (synchronises the device).  NULL is a no-op. */
+mach_status mach_plan_destroy(mach_plan p);
+
+/* Static, NUL-terminated description of a status code. */
+const char *mach_status_string(mach_status s);
+
+/* ---- inspection (used by the parity tests; not needed for beamforming) --------- */
+
+typedef struct {
+    char variant[40];        /* kernel variant name                                    */
+    int32_t frames_per_lane; /* frames accumulated by one thread                       */
+    int32_t lanes_per_voxel; /* threads sharing one voxel (frames or channel slices)   */
+    int32_t voxels_per_cta;  /* voxels of one thread block                             */
+    int32_t threads_per_cta;
+    int32_t tile[3];         /* voxel tile of one block (x, y, z)                      */
+    int32_t frame_tiles;     /* blocks along the frame axis                            */
+    int64_t ctas;            /* blocks of one run                                      */
+    int64_t smem_bytes;      /* dynamic shared memory per block                        */
+    int64_t device_bytes;    /* device memory held by the plan                         */
+} mach_plan_info;
+
+mach_status mach_plan_get_info(mach_plan p, mach_plan_info *info);
+
+/* Copy the plan's transmit delay table, float32 [n_tx][n_vox] in samples
+ * (s_tx = ((u.p)/c - t0) fs, or (arrival - t0) fs), into out_dev.  Stream-ordered. */
+mach_status mach_plan_tx_table(mach_plan p, float *out_dev, void *stream);
+
+/* Evaluate the per-term quantities exactly as the DAS kernels do, for n voxels:
+ * outputs [n][n_elem][n_tx]: i0 (int32, -1 when the term is dropped by the range or
+ * aperture rule), w = s - i0 (float32), complex weight a e^{j phi} (float32 pairs).
+ * vox_idx_dev: device int64 [n].  Any output may be NULL.  Stream-ordered. */
+mach_status mach_das_terms(mach_plan p, const int64_t *vox_idx_dev, int64_t n,
+                           int32_t *i0_dev, float *w_dev, float *cw_dev, void *stream);
+
+/* Library version string, e.g. "mach-gb300 0.1.0 sm_103a". */
+const char *mach_version(void);
+
+/* Test hook: make the n-th device allocation from now fail (n >= 1); n <= 0 disarms.
+ * Lets tests exercise the MACH_ERR_OOM clean-up path without exhausting memory. */
+void mach_debug_fail_alloc_after(int32_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MACH_H */

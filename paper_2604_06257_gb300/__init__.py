@@ -1,0 +1,385 @@
+"""GB300 delay-and-sum beamforming (mach, arXiv 2604.06257) -- Python binding.
+
+A thin ctypes layer over ``libmach_gb300.so`` (the C ABI in ``include/mach.h``).  It only
+marshals arguments: every step of the beamforming runs in the library's CUDA kernels.
+There is no CPU fallback; importing works without a GPU, but any call needs the built
+library and a CUDA device and raises otherwise.
+
+Functions carry the C names (``mach_das_plan``, ``mach_das_run``, ``mach_power_doppler``,
+``mach_plan_destroy``, ``mach_status_string`` ...).  ``Plan`` is a small convenience
+wrapper that owns a plan handle and accepts torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import counts  # noqa: F401  (host-side Eq. 1 / Eq. 2 accounting)
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmach_gb300.so")
+
+MACH_OK, MACH_ERR_INVALID_ARG, MACH_ERR_CUDA, MACH_ERR_OOM, MACH_ERR_UNSUPPORTED, MACH_ERR_TIMEOUT = range(6)
+APOD = {"none": 0, "boxcar": 1, "hann": 2, "gauss": 3}
+IQ_DTYPE = {"c64": 0, "f16x2": 1}
+
+EXPORTS = ("mach_das_plan", "mach_das_run", "mach_power_doppler", "mach_plan_destroy",
+           "mach_status_string", "mach_plan_get_info", "mach_plan_tx_table", "mach_das_terms",
+           "mach_version", "mach_debug_fail_alloc_after")
+
+
+class MachError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = int(status)
+        super().__init__(f"{where}: {mach_status_string(status)} ({status})")
+
+
+class mach_das_desc(C.Structure):
+    _fields_ = [
+        ("ndim", C.c_int32), ("n_elem", C.c_int32), ("elem_pos", C.c_void_p),
+        ("n_vox", C.c_int64), ("vox_pos", C.c_void_p),
+        ("grid_dims", C.c_int32 * 3), ("grid_origin", C.c_double * 3), ("grid_step", C.c_double * 3),
+        ("n_tx", C.c_int32), ("tx_angles", C.c_void_p), ("tx_table_dev", C.c_void_p),
+        ("fs", C.c_double), ("fc", C.c_double), ("c", C.c_double), ("t0", C.c_double),
+        ("f_number", C.c_double), ("apod", C.c_int32), ("n_samples", C.c_int32),
+        ("n_frames", C.c_int32), ("iq_dtype", C.c_int32),
+    ]
+
+
+class mach_plan_info(C.Structure):
+    _fields_ = [
+        ("variant", C.c_char * 40), ("frames_per_lane", C.c_int32), ("lanes_per_voxel", C.c_int32),
+        ("voxels_per_cta", C.c_int32), ("threads_per_cta", C.c_int32), ("tile", C.c_int32 * 3),
+        ("frame_tiles", C.c_int32), ("ctas", C.c_int64), ("smem_bytes", C.c_int64),
+        ("device_bytes", C.c_int64),
+    ]
+
+    def as_dict(self):
+        return {"variant": self.variant.decode(), "frames_per_lane": self.frames_per_lane,
+                "lanes_per_voxel": self.lanes_per_voxel, "voxels_per_cta": self.voxels_per_cta,
+                "threads_per_cta": self.threads_per_cta, "tile": list(self.tile),
+                "frame_tiles": self.frame_tiles, "ctas": self.ctas, "smem_bytes": self.smem_bytes,
+                "device_bytes": self.device_bytes}
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2604_06257_gb300/build.py "
+                               "(there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        L.mach_das_plan.argtypes = [C.POINTER(mach_das_desc), vp, C.POINTER(vp)]
+        L.mach_das_run.argtypes = [vp, vp, vp, vp]
+        L.mach_power_doppler.argtypes = [vp, vp, vp, vp, vp]
+        L.mach_plan_destroy.argtypes = [vp]
+        L.mach_status_string.argtypes = [C.c_int]
+        L.mach_status_string.restype = C.c_char_p
+        L.mach_plan_get_info.argtypes = [vp, C.POINTER(mach_plan_info)]
+        L.mach_plan_tx_table.argtypes = [vp, vp, vp]
+        L.mach_das_terms.argtypes = [vp, vp, i64, vp, vp, vp, vp]
+        L.mach_version.restype = C.c_char_p
+        L.mach_debug_fail_alloc_after.argtypes = [i32]
+        L.mach_debug_fail_alloc_after.restype = None
+        for f in ("mach_das_plan", "mach_das_run", "mach_power_doppler", "mach_plan_destroy",
+                  "mach_plan_get_info", "mach_plan_tx_table", "mach_das_terms"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+# ---- raw ABI wrappers (same names as the C entry points) ---------------------------
+
+def mach_status_string(status: int) -> str:
+    return lib().mach_status_string(int(status)).decode()
+
+
+def mach_version() -> str:
+    return lib().mach_version().decode()
+
+
+def mach_debug_fail_alloc_after(n: int) -> None:
+    lib().mach_debug_fail_alloc_after(int(n))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dev_ptr(t, what, dtype=None, numel=None):
+    """Device pointer of a contiguous CUDA tensor (or an int address)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{what} must be {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{what} has {t.numel()} elements, expected {numel}")
+    return t.data_ptr()
+
+
+class _HostArrays:
+    """Keeps the host arrays a descriptor points into alive."""
+
+    def __init__(self):
+        self.keep = []
+
+    def f32(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        self.keep.append(a)
+        return a.ctypes.data
+
+    def f64(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        self.keep.append(a)
+        return a.ctypes.data
+
+
+def make_desc(*, ndim: int, elem_pos, fs: float, fc: float, c: float, n_samples: int,
+              n_frames: int, tx_angles=None, tx_table_dev=None, t0: float = 0.0,
+              f_number: float = 1.0, apod: str = "boxcar", vox_pos=None,
+              grid_dims: Optional[Sequence[int]] = None, grid_origin=(0.0, 0.0, 0.0),
+              grid_step=(0.0, 0.0, 0.0), iq_dtype: str = "c64"):
+    """Build a ``mach_das_desc`` (plus the host arrays it references)."""
+    h = _HostArrays()
+    d = mach_das_desc()
+    d.ndim = ndim
+    ep = np.asarray(elem_pos)
+    d.n_elem = ep.shape[0]
+    d.elem_pos = h.f32(ep)
+    if vox_pos is not None:
+        vp = np.asarray(vox_pos)
+        d.n_vox = vp.shape[0]
+        d.vox_pos = h.f32(vp)
+    else:
+        d.grid_dims = (C.c_int32 * 3)(*grid_dims)
+        d.grid_origin = (C.c_double * 3)(*grid_origin)
+        d.grid_step = (C.c_double * 3)(*grid_step)
+        d.n_vox = int(np.prod(grid_dims))
+    if tx_angles is not None:
+        ta = np.asarray(tx_angles, dtype=np.float64).reshape(-1, 2)
+        d.n_tx = ta.shape[0]
+        d.tx_angles = h.f64(ta)
+    if tx_table_dev is not None:
+        d.tx_table_dev = _dev_ptr(tx_table_dev, "tx_table_dev", None)
+        if tx_angles is None:
+            d.n_tx = tx_table_dev.shape[0]
+    d.fs, d.fc, d.c, d.t0, d.f_number = fs, fc, c, t0, f_number
+    d.apod = APOD[apod] if isinstance(apod, str) else int(apod)
+    d.n_samples, d.n_frames = n_samples, n_frames
+    d.iq_dtype = IQ_DTYPE[iq_dtype] if isinstance(iq_dtype, str) else int(iq_dtype)
+    return d, h
+
+
+def mach_das_plan(desc, stream=None) -> int:
+    """Create a plan; returns the opaque handle (int).  Raises MachError."""
+    h = C.c_void_p()
+    st = lib().mach_das_plan(C.byref(desc), _stream_ptr(stream), C.byref(h))
+    if st != MACH_OK:
+        raise MachError(st, "mach_das_plan")
+    return h.value
+
+
+def mach_das_run(plan: int, iq, y, stream=None) -> None:
+    st = lib().mach_das_run(plan, _dev_ptr(iq, "iq"), _dev_ptr(y, "y"), _stream_ptr(stream))
+    if st != MACH_OK:
+        raise MachError(st, "mach_das_run")
+
+
+def mach_power_doppler(plan: int, iq, pd, y=None, stream=None) -> None:
+    st = lib().mach_power_doppler(plan, _dev_ptr(iq, "iq"), _dev_ptr(pd, "pd"), _dev_ptr(y, "y"),
+                                  _stream_ptr(stream))
+    if st != MACH_OK:
+        raise MachError(st, "mach_power_doppler")
+
+
+def mach_plan_destroy(plan: int) -> None:
+    st = lib().mach_plan_destroy(plan)
+    if st != MACH_OK:
+        raise MachError(st, "mach_plan_destroy")
+
+
+def mach_plan_get_info(plan: int) -> dict:
+    info = mach_plan_info()
+    st = lib().mach_plan_get_info(plan, C.byref(info))
+    if st != MACH_OK:
+        raise MachError(st, "mach_plan_get_info")
+    return info.as_dict()
+
+
+def mach_plan_tx_table(plan: int, out, stream=None) -> None:
+    st = lib().mach_plan_tx_table(plan, _dev_ptr(out, "out"), _stream_ptr(stream))
+    if st != MACH_OK:
+        raise MachError(st, "mach_plan_tx_table")
+
+
+def mach_das_terms(plan: int, vox_idx, i0=None, w=None, cw=None, stream=None) -> None:
+    st = lib().mach_das_terms(plan, _dev_ptr(vox_idx, "vox_idx"), int(vox_idx.numel()),
+                              _dev_ptr(i0, "i0"), _dev_ptr(w, "w"), _dev_ptr(cw, "cw"),
+                              _stream_ptr(stream))
+    if st != MACH_OK:
+        raise MachError(st, "mach_das_terms")
+
+
+# ---- convenience wrapper ------------------------------------------------------------
+
+class Plan:
+    """Owns a plan handle.  ``run`` / ``power_doppler`` take CUDA tensors (complex64 or
+    float16 [..., 2] IQ [T, C, S, F]) and return CUDA tensors; given CPU tensors they
+    stage through reusable device buffers and return CPU tensors."""
+
+    def __init__(self, stream=None, **desc_kw):
+        import torch
+        self.desc, self._host = make_desc(**desc_kw)
+        self.n_vox = int(self.desc.n_vox)
+        self.n_frames = int(self.desc.n_frames)
+        self.iq_dtype = "f16x2" if self.desc.iq_dtype == 1 else "c64"
+        self.iq_shape = (int(self.desc.n_tx), int(self.desc.n_elem), int(self.desc.n_samples),
+                         self.n_frames)
+        self.handle = mach_das_plan(self.desc, stream)
+        self._stage = {}
+        self._torch = torch
+
+    # geometry ----------------------------------------------------------------
+    def info(self) -> dict:
+        return mach_plan_get_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mach_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # checks --------------------------------------------------------------------
+    def _check_iq(self, iq):
+        torch = self._torch
+        if self.iq_dtype == "c64":
+            if iq.dtype != torch.complex64 or tuple(iq.shape) != self.iq_shape:
+                raise ValueError(f"iq must be complex64 {self.iq_shape}, got {iq.dtype} {tuple(iq.shape)}")
+        else:
+            if iq.dtype != torch.float16 or tuple(iq.shape) != self.iq_shape + (2,):
+                raise ValueError(f"iq must be float16 {self.iq_shape + (2,)}")
+
+    def _buf(self, name, shape, dtype):
+        torch = self._torch
+        b = self._stage.get(name)
+        if b is None or b.shape != shape or b.dtype != dtype:
+            b = torch.empty(shape, dtype=dtype, device="cuda")
+            self._stage[name] = b
+        return b
+
+    # compute -------------------------------------------------------------------
+    def run(self, iq, y=None, stream=None):
+        """Complex frames y [V, F] (complex64)."""
+        torch = self._torch
+        self._check_iq(iq)
+        host = not iq.is_cuda
+        if host:
+            dev = self._buf("iq", tuple(iq.shape), iq.dtype)
+            dev.copy_(iq, non_blocking=True)
+            iq = dev
+        out = y if y is not None else (self._buf("y", (self.n_vox, self.n_frames), torch.complex64)
+                                       if host else torch.empty((self.n_vox, self.n_frames),
+                                                                dtype=torch.complex64, device=iq.device))
+        mach_das_run(self.handle, iq, out, stream)
+        return out.cpu() if host else out
+
+    def power_doppler(self, iq, pd=None, y=None, want_y=False, stream=None):
+        """Power Doppler pd [V] (float32) and, if requested, the frames y [V, F]."""
+        torch = self._torch
+        self._check_iq(iq)
+        host = not iq.is_cuda
+        if host:
+            dev = self._buf("iq", tuple(iq.shape), iq.dtype)
+            dev.copy_(iq, non_blocking=True)
+            iq = dev
+        if pd is None:
+            pd = (self._buf("pd", (self.n_vox,), torch.float32) if host else
+                  torch.empty((self.n_vox,), dtype=torch.float32, device=iq.device))
+        if y is None and want_y:
+            y = (self._buf("y", (self.n_vox, self.n_frames), torch.complex64) if host else
+                 torch.empty((self.n_vox, self.n_frames), dtype=torch.complex64, device=iq.device))
+        mach_power_doppler(self.handle, iq, pd, y, stream)
+        if host:
+            return pd.cpu(), (y.cpu() if y is not None else None)
+        return pd, y
+
+    def power_doppler_host(self, iq_host, pd_host, y_host=None, stream=None):
+        """Host buffers in and out (pinned memory recommended): copies the IQ to the
+        device, beamforms, copies Power Doppler (and the frames, if ``y_host`` is given)
+        back, and returns once the results are in host memory."""
+        torch = self._torch
+        self._check_iq(iq_host)
+        s = torch.cuda.current_stream() if stream is None else stream
+        with torch.cuda.stream(s):
+            dev = self._buf("iq", tuple(iq_host.shape), iq_host.dtype)
+            dev.copy_(iq_host, non_blocking=True)
+            pd_d = self._buf("pd", (self.n_vox,), torch.float32)
+            y_d = (self._buf("y", (self.n_vox, self.n_frames), torch.complex64)
+                   if y_host is not None else None)
+            mach_power_doppler(self.handle, dev, pd_d, y_d, s)
+            pd_host.copy_(pd_d, non_blocking=True)
+            if y_host is not None:
+                y_host.copy_(y_d, non_blocking=True)
+        s.synchronize()
+        return pd_host, y_host
+
+    def tx_table(self):
+        torch = self._torch
+        out = torch.empty((self.iq_shape[0], self.n_vox), dtype=torch.float32, device="cuda")
+        mach_plan_tx_table(self.handle, out)
+        return out
+
+    def terms(self, vox_idx):
+        """(i0 int32, w float32, cw complex64) of shape [n, C, T], as the kernels compute them."""
+        torch = self._torch
+        idx = torch.as_tensor(vox_idx, dtype=torch.int64).cuda().contiguous()
+        n, T, Cn = idx.numel(), self.iq_shape[0], self.iq_shape[1]
+        i0 = torch.empty((n, Cn, T), dtype=torch.int32, device="cuda")
+        w = torch.empty((n, Cn, T), dtype=torch.float32, device="cuda")
+        cw = torch.empty((n, Cn, T, 2), dtype=torch.float32, device="cuda")
+        mach_das_terms(self.handle, idx, i0, w, cw)
+        return i0, w, torch.view_as_complex(cw)
+
+
+def plan_kwargs(acq) -> dict:
+    """Keyword arguments of ``Plan`` / ``make_desc`` from an object with the attributes of
+    an acquisition description (ndim, elem_pos, tx_angles, fs, fc, c, t0, f_number, apod,
+    n_samples, n_frames, grid_dims/grid_origin/grid_step or vox_pos, iq_dtype)."""
+    kw = dict(ndim=acq.ndim, elem_pos=acq.elem_pos, tx_angles=acq.tx_angles, fs=acq.fs, fc=acq.fc,
+              c=acq.c, t0=acq.t0, f_number=acq.f_number, apod=acq.apod, n_samples=acq.n_samples,
+              n_frames=acq.n_frames, iq_dtype=acq.iq_dtype)
+    if acq.vox_pos is not None:
+        kw["vox_pos"] = acq.vox_pos
+    else:
+        kw.update(grid_dims=acq.grid_dims, grid_origin=acq.grid_origin, grid_step=acq.grid_step)
+    return kw

@@ -1,0 +1,92 @@
+// das_term.cuh -- per-(voxel, element, transmit) delay, index and weight.
+//
+// The index decision is taken in float32 with one fixed operation sequence (every
+// step an explicitly rounded intrinsic, so the compiler cannot fuse or reorder it):
+//   d   = v - e                                   (sample units, per axis)
+//   rx  = sqrt_rn(fma(dx,dx, fma(dy,dy, dz*dz)))  receive path, Sec. 4.3 "on the fly"
+//   s   = s_tx + rx                               s_tx from the per-plan table
+//   term kept iff inside the aperture and 0 <= s < S-1   (range rule: both taps exist)
+//   i0  = floor(s), w = s - i0 (exact)            linear interpolation, Sec. 4.1
+// The window and phase are float32 approximations (errors ~1e-7, far below the
+// interpolation's own quantisation):
+//   aperture: rho = sqrt_rn(fma(dx,dx, dy*dy)); kept iff dz > 0 and rho*2F# <= dz;
+//             window of t = rho F#/dz: boxcar 1, Hann cos^2(pi t), Gaussian exp(-8 t^2)
+//   phase:    fc (t0 + s/fs) cycles = frac(fc t0) + i0 frac(fc/fs) + w fc/fs, with the
+//             first two terms in 32-bit fixed point (exact wrap-around modulo one cycle)
+//             so that large sample indices lose no phase accuracy.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "mach_internal.h"
+
+namespace mach {
+
+struct TermGeo {
+  float rx;   // receive delay, samples
+  float a;    // window value, or -1 when the element is outside the aperture
+};
+
+__device__ __forceinline__ TermGeo term_geometry(const float4 v, const float4 e,
+                                                 const DasParams& p) {
+  const float dx = __fsub_rn(v.x, e.x);
+  const float dy = __fsub_rn(v.y, e.y);
+  const float dz = __fsub_rn(v.z, e.z);
+  TermGeo g;
+  g.rx = __fsqrt_rn(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz))));
+  if (p.apod == MACH_APOD_NONE) {
+    g.a = 1.0f;
+    return g;
+  }
+  const float rho = __fsqrt_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)));
+  if (!(dz > 0.0f && __fmul_rn(rho, p.two_f) <= dz)) {
+    g.a = -1.0f;
+    return g;
+  }
+  if (p.apod == MACH_APOD_BOXCAR) {
+    g.a = 1.0f;
+    return g;
+  }
+  const float t = __fdividef(rho * p.f_num, dz);   // in [0, 1/2]
+  if (p.apod == MACH_APOD_HANN) {
+    const float cp = __cosf(3.14159265358979f * t);
+    g.a = cp * cp;
+  } else {
+    g.a = __expf(-8.0f * t * t);
+  }
+  return g;
+}
+
+// Record of one term: (a cos phi, a sin phi, w, i0 bits); i0 = -1 marks a dropped term.
+__device__ __forceinline__ float4 term_record(const float s_tx, const TermGeo g,
+                                              const DasParams& p) {
+  const float s = __fadd_rn(s_tx, g.rx);
+  if (!(g.a >= 0.0f && s >= 0.0f && s < p.s_max)) return make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+  const float fl = floorf(s);
+  const int i0 = static_cast<int>(fl);
+  const float w = __fsub_rn(s, fl);
+  const uint32_t ph = p.phase_Phi + static_cast<uint32_t>(i0) * p.phase_R;
+  float x = __fmaf_rn(w, p.r_f, static_cast<float>(static_cast<int32_t>(ph)) * 2.3283064365386963e-10f);
+  x -= rintf(x);                                   // cycles in [-1/2, 1/2]
+  float sn, cs;
+  __sincosf(6.28318530717958648f * x, &sn, &cs);
+  return make_float4(g.a * cs, g.a * sn, w, __int_as_float(i0));
+}
+
+// Voxel index of slot q of tile `tile`, or -1 past the grid edge (ragged tiles).
+__device__ __forceinline__ int64_t tile_voxel(const DasParams& p, int64_t tile, int q) {
+  const int qx = q % p.tile_x;
+  const int qr = q / p.tile_x;
+  const int qy = qr % p.tile_y;
+  const int qz = qr / p.tile_y;
+  const int64_t bx = tile % p.tiles_x;
+  const int64_t br = tile / p.tiles_x;
+  const int64_t by = br % p.tiles_y;
+  const int64_t bz = br / p.tiles_y;
+  const int64_t gx = bx * p.tile_x + qx, gy = by * p.tile_y + qy, gz = bz * p.tile_z + qz;
+  if (gx >= p.nx || gy >= p.ny || gz >= p.nz) return -1;
+  return gx + static_cast<int64_t>(p.nx) * (gy + static_cast<int64_t>(p.ny) * gz);
+}
+
+}  // namespace mach

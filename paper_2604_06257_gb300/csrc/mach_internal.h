@@ -1,0 +1,87 @@
+// mach_internal.h -- plan state shared between the host plan code and the kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mach.h"
+
+namespace mach {
+
+// Kernel variants.  "frame lanes" kernels put frames on the lanes of a warp (the
+// paper's frame-contiguous layout, Sec. 4.4); "channel lanes" kernels put a voxel's
+// elements on the lanes (for ensembles too short to fill a warp, Sec. 4.6 notes the
+// loss of coalescing below 16 frames).
+enum Variant : int32_t {
+  V_CH_C64 = 0,      // channel lanes, F <= 4, complex64
+  V_F16_C64,         // frame lanes, 16-frame tile, complex64 (F even)
+  V_F32_C64,         // frame lanes, 32-frame tile, complex64 (F even)
+  V_F64_C64,         // frame lanes, 64-frame tile, complex64 (F even)
+  V_S32_C64,         // frame lanes, 32-frame tile, scalar loads (any F)
+  V_CH_H16,          // channel lanes, F <= 4, float16 pairs
+  V_F32_H16,         // frame lanes, 32-frame tile, float16 pairs (F % 4 == 0)
+  V_F64_H16,         // frame lanes, 64-frame tile, float16 pairs (F % 4 == 0)
+  V_S32_H16,         // frame lanes, 32-frame tile, scalar loads (any F)
+  V_COUNT
+};
+
+struct VariantShape {
+  const char* name;
+  int frames_per_lane;   // frames one thread accumulates
+  int lanes_per_voxel;   // frame lanes per voxel, or channel slices per voxel
+  int voxels_per_warp;
+  int frame_tile;        // frames covered by one block
+  int warps;             // warps per block
+  bool channel_lanes;
+};
+
+const VariantShape& variant_shape(Variant v);
+
+// Everything a DAS kernel reads, passed by value.
+struct DasParams {
+  const float4* vox;    // [V] voxel position in sample units (x, y, z, 0)
+  const float4* elem;   // [C] element position in sample units
+  const float* tx;      // [T][V] transmit delay in samples
+  const void* iq;       // [T][C][S][F] complex (float2 or half2)
+  float2* y;            // [V][F] or nullptr
+  float* pd;            // [V] or nullptr
+  float* pd_part;       // [frame_tiles][V] scratch when frame_tiles > 1
+  int64_t V;
+  int C, T, S, F;
+  int nx, ny, nz;       // voxel index space (a list is nx = V, ny = nz = 1)
+  int tile_x, tile_y, tile_z;
+  int tiles_x, tiles_y, tiles_z;
+  int apod;
+  float two_f;          // (float)(2 F#)
+  float f_num;          // (float)F#
+  float s_max;          // (float)(S - 1): a term needs 0 <= s < s_max
+  float r_f;            // (float)(fc / fs)
+  uint32_t phase_R;     // round(2^32 frac(fc / fs))
+  uint32_t phase_Phi;   // round(2^32 frac(fc t0))
+  int frame_tiles;
+};
+
+// Tables built once per plan (kernel K1).
+struct TableParams {
+  const float* raw_vox;     // [V][3] metres (list) or nullptr (grid)
+  const double* u;          // [T][3] direction cosines (plane waves) or nullptr
+  const float* tx_seconds;  // [T][V] user arrival times or nullptr
+  double k;                 // fs / c
+  double t0fs;              // t0 * fs
+  double fs;
+  double origin[3], step[3];
+  int nx, ny, nz;
+  int64_t V;
+  int T;
+  float4* vox_out;
+  float* tx_out;
+};
+
+cudaError_t launch_tables(const TableParams& tp, cudaStream_t s);
+cudaError_t launch_das(const DasParams& p, Variant v, cudaStream_t s);
+cudaError_t launch_terms(const DasParams& p, const int64_t* vox_idx, int64_t n, int32_t* i0,
+                         float* w, float* cw, cudaStream_t s);
+size_t das_smem_bytes(Variant v);
+
+}  // namespace mach

@@ -1,0 +1,379 @@
+// plan.cpp -- the C ABI: argument validation, plan construction (Sec. 4.3 precompute),
+// kernel-variant selection and the run entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mach.h"
+#include "mach_internal.h"
+
+using namespace mach;
+
+struct mach_plan_s {
+  mach_das_desc d{};          // copy; pointer fields cleared
+  int device = 0;
+  Variant variant = V_COUNT;
+  DasParams base{};           // everything but iq / y / pd
+  float4* d_vox = nullptr;
+  float4* d_elem = nullptr;
+  float* d_tx = nullptr;
+  float* d_pd_part = nullptr;
+  int64_t device_bytes = 0;
+};
+
+namespace {
+
+int g_fail_alloc_countdown = 0;   // test hook: > 0 -> the n-th allocation fails
+
+mach_status dev_alloc(void** p, size_t bytes, int64_t* total) {
+  *p = nullptr;
+  if (g_fail_alloc_countdown > 0 && --g_fail_alloc_countdown == 0) return MACH_ERR_OOM;
+  if (bytes == 0) bytes = 16;
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return MACH_ERR_OOM;
+  }
+  if (e != cudaSuccess) return MACH_ERR_CUDA;
+  *total += static_cast<int64_t>(bytes);
+  return MACH_OK;
+}
+
+bool finite3(const float* p, int64_t n) {
+  for (int64_t i = 0; i < 3 * n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+mach_status validate(const mach_das_desc* d) {
+  if (!d) return MACH_ERR_INVALID_ARG;
+  if (d->ndim != 2 && d->ndim != 3) return MACH_ERR_INVALID_ARG;
+  if (d->n_elem < 1 || !d->elem_pos) return MACH_ERR_INVALID_ARG;
+  if (d->n_tx < 1 || (!d->tx_angles && !d->tx_table_dev)) return MACH_ERR_INVALID_ARG;
+  if (!(d->fs > 0.0) || !std::isfinite(d->fs) || !(d->c > 0.0) || !std::isfinite(d->c))
+    return MACH_ERR_INVALID_ARG;
+  if (!(d->fc >= 0.0) || !std::isfinite(d->fc) || !std::isfinite(d->t0)) return MACH_ERR_INVALID_ARG;
+  if (!(d->f_number >= 0.0) || !std::isfinite(d->f_number)) return MACH_ERR_INVALID_ARG;
+  if (d->apod < MACH_APOD_NONE || d->apod > MACH_APOD_GAUSS) return MACH_ERR_INVALID_ARG;
+  if (d->iq_dtype != MACH_IQ_C64 && d->iq_dtype != MACH_IQ_F16X2) return MACH_ERR_INVALID_ARG;
+  if (d->n_samples < 2 || d->n_samples > (1 << 24)) return MACH_ERR_INVALID_ARG;
+  if (d->n_frames < 1) return MACH_ERR_INVALID_ARG;
+  // per-(t, c) slab offsets are computed in 64 bits, but one slab must stay indexable
+  if (static_cast<int64_t>(d->n_samples) * d->n_frames > (int64_t{1} << 31) - 1) return MACH_ERR_UNSUPPORTED;
+  if (!finite3(d->elem_pos, d->n_elem)) return MACH_ERR_INVALID_ARG;
+  int64_t V;
+  if (d->vox_pos) {
+    if (d->n_vox < 1) return MACH_ERR_INVALID_ARG;
+    V = d->n_vox;
+    if (!finite3(d->vox_pos, V)) return MACH_ERR_INVALID_ARG;
+  } else {
+    for (int k = 0; k < 3; ++k) {
+      if (d->grid_dims[k] < 1) return MACH_ERR_INVALID_ARG;
+      if (!std::isfinite(d->grid_origin[k]) || !std::isfinite(d->grid_step[k])) return MACH_ERR_INVALID_ARG;
+    }
+    V = static_cast<int64_t>(d->grid_dims[0]) * d->grid_dims[1] * d->grid_dims[2];
+    if (d->n_vox != 0 && d->n_vox != V) return MACH_ERR_INVALID_ARG;
+  }
+  if (V > (int64_t{1} << 40)) return MACH_ERR_UNSUPPORTED;
+  if (d->tx_angles)
+    for (int t = 0; t < 2 * d->n_tx; ++t)
+      if (!std::isfinite(d->tx_angles[t])) return MACH_ERR_INVALID_ARG;
+  if (d->ndim == 2) {   // a 2D acquisition lives in the plane y = 0
+    for (int c = 0; c < d->n_elem; ++c)
+      if (d->elem_pos[3 * c + 1] != 0.0f) return MACH_ERR_INVALID_ARG;
+    if (d->tx_angles && !d->tx_table_dev)
+      for (int t = 0; t < d->n_tx; ++t)
+        if (d->tx_angles[2 * t + 1] != 0.0) return MACH_ERR_INVALID_ARG;
+    if (d->vox_pos) {
+      for (int64_t v = 0; v < V; ++v)
+        if (d->vox_pos[3 * v + 1] != 0.0f) return MACH_ERR_INVALID_ARG;
+    } else if (d->grid_dims[1] != 1 || d->grid_origin[1] != 0.0) {
+      return MACH_ERR_INVALID_ARG;
+    }
+  }
+  return MACH_OK;
+}
+
+Variant pick_variant(int iq_dtype, int F) {
+  if (iq_dtype == MACH_IQ_C64) {
+    if (F <= 4) return V_CH_C64;
+    if (F % 2 == 0) return F <= 16 ? V_F16_C64 : (F <= 32 ? V_F32_C64 : V_F64_C64);
+    return V_S32_C64;
+  }
+  if (F <= 4) return V_CH_H16;
+  if (F % 4 == 0) return F <= 32 ? V_F32_H16 : V_F64_H16;
+  return V_S32_H16;
+}
+
+// Voxel tile of one block: compact boxes so that the voxels sharing a block (and the
+// L1 cache) read overlapping sample windows of each element.
+void pick_tile(int n, int nx, int ny, int nz, bool list, int tile[3]) {
+  if (list || (ny == 1 && nz == 1)) {
+    tile[0] = n; tile[1] = 1; tile[2] = 1;
+    return;
+  }
+  if (ny == 1) {   // 2D x-z grid
+    const int tx = std::min(16, n);
+    tile[0] = tx; tile[1] = 1; tile[2] = n / tx;
+    return;
+  }
+  int tx = 8, ty = 4;
+  if (n < 32) { tx = 4; ty = 2; }
+  tile[0] = tx; tile[1] = ty; tile[2] = n / (tx * ty);
+}
+
+uint32_t fixed_cycles(double cycles) {   // round(2^32 frac(cycles))
+  double f = cycles - std::floor(cycles);
+  double r = std::nearbyint(f * 4294967296.0);
+  if (r >= 4294967296.0) r -= 4294967296.0;
+  return static_cast<uint32_t>(r);
+}
+
+void release(mach_plan_s* p) {
+  if (!p) return;
+  cudaFree(p->d_vox);
+  cudaFree(p->d_elem);
+  cudaFree(p->d_tx);
+  cudaFree(p->d_pd_part);
+  delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mach_status_string(mach_status s) {
+  switch (s) {
+    case MACH_OK: return "ok";
+    case MACH_ERR_INVALID_ARG: return "invalid argument";
+    case MACH_ERR_CUDA: return "CUDA error";
+    case MACH_ERR_OOM: return "out of device memory";
+    case MACH_ERR_UNSUPPORTED: return "unsupported configuration";
+    case MACH_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+const char* mach_version(void) { return "mach-gb300 0.1.0 sm_103a"; }
+
+void mach_debug_fail_alloc_after(int32_t n) { g_fail_alloc_countdown = n > 0 ? n : 0; }
+
+mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) {
+  if (!out) return MACH_ERR_INVALID_ARG;
+  *out = nullptr;
+  mach_status st = validate(d);
+  if (st != MACH_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  const int C = d->n_elem, T = d->n_tx, S = d->n_samples, F = d->n_frames;
+  const bool list = d->vox_pos != nullptr;
+  const int64_t V = list ? d->n_vox
+                         : static_cast<int64_t>(d->grid_dims[0]) * d->grid_dims[1] * d->grid_dims[2];
+  const Variant var = pick_variant(d->iq_dtype, F);
+  const VariantShape& shp = variant_shape(var);
+  const int frame_tiles = (F + shp.frame_tile - 1) / shp.frame_tile;
+  const int per_cta = shp.voxels_per_warp * shp.warps;
+  if (frame_tiles > 65535) return MACH_ERR_UNSUPPORTED;   // grid y limit
+
+  // host-side size check before touching the device
+  const size_t need = static_cast<size_t>(V) * (sizeof(float4) + sizeof(float) * T) + sizeof(float4) * C +
+                      (frame_tiles > 1 ? sizeof(float) * V * frame_tiles : 0) +
+                      (list ? sizeof(float) * 3 * V : 0) + sizeof(double) * 3 * T;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return MACH_ERR_CUDA;
+  }
+  if (need > free_b) return MACH_ERR_OOM;
+
+  mach_plan_s* p = new (std::nothrow) mach_plan_s();
+  if (!p) return MACH_ERR_OOM;
+  p->d = *d;
+  p->d.elem_pos = nullptr;
+  p->d.vox_pos = nullptr;
+  p->d.tx_angles = nullptr;
+  p->d.tx_table_dev = nullptr;
+  p->d.n_vox = V;
+  p->variant = var;
+  cudaGetDevice(&p->device);
+
+  const double k = d->fs / d->c;
+  const double t0fs = d->t0 * d->fs;
+  std::vector<float4> elem(C);
+  for (int c = 0; c < C; ++c)
+    elem[c] = make_float4(static_cast<float>(static_cast<double>(d->elem_pos[3 * c]) * k),
+                          static_cast<float>(static_cast<double>(d->elem_pos[3 * c + 1]) * k),
+                          static_cast<float>(static_cast<double>(d->elem_pos[3 * c + 2]) * k), 0.0f);
+  std::vector<double> u;
+  if (!d->tx_table_dev) {
+    u.resize(3 * static_cast<size_t>(T));
+    for (int t = 0; t < T; ++t) {
+      const double az = d->tx_angles[2 * t], el = d->tx_angles[2 * t + 1];
+      u[3 * t] = std::sin(az) * std::cos(el);
+      u[3 * t + 1] = std::sin(el);
+      u[3 * t + 2] = std::cos(az) * std::cos(el);
+    }
+  }
+
+  float* d_raw = nullptr;
+  double* d_u = nullptr;
+  int64_t scratch_bytes = 0;
+  auto fail = [&](mach_status e) {
+    cudaFree(d_raw);
+    cudaFree(d_u);
+    release(p);
+    return e;
+  };
+  if ((st = dev_alloc(reinterpret_cast<void**>(&p->d_vox), sizeof(float4) * V, &p->device_bytes)) != MACH_OK) return fail(st);
+  if ((st = dev_alloc(reinterpret_cast<void**>(&p->d_elem), sizeof(float4) * C, &p->device_bytes)) != MACH_OK) return fail(st);
+  if ((st = dev_alloc(reinterpret_cast<void**>(&p->d_tx), sizeof(float) * T * V, &p->device_bytes)) != MACH_OK) return fail(st);
+  if (frame_tiles > 1 &&
+      (st = dev_alloc(reinterpret_cast<void**>(&p->d_pd_part), sizeof(float) * frame_tiles * V, &p->device_bytes)) != MACH_OK)
+    return fail(st);
+  if (list && (st = dev_alloc(reinterpret_cast<void**>(&d_raw), sizeof(float) * 3 * V, &scratch_bytes)) != MACH_OK)
+    return fail(st);
+  if (!u.empty() && (st = dev_alloc(reinterpret_cast<void**>(&d_u), sizeof(double) * u.size(), &scratch_bytes)) != MACH_OK)
+    return fail(st);
+
+  if (cudaMemcpyAsync(p->d_elem, elem.data(), sizeof(float4) * C, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return fail(MACH_ERR_CUDA);
+  if (list && cudaMemcpyAsync(d_raw, d->vox_pos, sizeof(float) * 3 * V, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return fail(MACH_ERR_CUDA);
+  if (d_u && cudaMemcpyAsync(d_u, u.data(), sizeof(double) * u.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return fail(MACH_ERR_CUDA);
+
+  TableParams tp{};
+  tp.raw_vox = d_raw;
+  tp.u = d_u;
+  tp.tx_seconds = d->tx_table_dev;
+  tp.k = k;
+  tp.t0fs = t0fs;
+  tp.fs = d->fs;
+  for (int a = 0; a < 3; ++a) {
+    tp.origin[a] = list ? 0.0 : d->grid_origin[a];
+    tp.step[a] = list ? 0.0 : d->grid_step[a];
+  }
+  tp.nx = list ? 1 : d->grid_dims[0];
+  tp.ny = list ? 1 : d->grid_dims[1];
+  tp.nz = list ? 1 : d->grid_dims[2];
+  tp.V = V;
+  tp.T = T;
+  tp.vox_out = p->d_vox;
+  tp.tx_out = p->d_tx;
+  if (launch_tables(tp, s) != cudaSuccess) return fail(MACH_ERR_CUDA);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(MACH_ERR_CUDA);
+  cudaFree(d_raw);
+  cudaFree(d_u);
+  d_raw = nullptr;
+  d_u = nullptr;
+
+  DasParams& b = p->base;
+  b.vox = p->d_vox;
+  b.elem = p->d_elem;
+  b.tx = p->d_tx;
+  b.pd_part = p->d_pd_part;
+  b.V = V;
+  b.C = C;
+  b.T = T;
+  b.S = S;
+  b.F = F;
+  if (list) {
+    b.nx = static_cast<int>(std::min<int64_t>(V, INT32_MAX));
+    b.ny = b.nz = 1;
+  } else {
+    b.nx = d->grid_dims[0];
+    b.ny = d->grid_dims[1];
+    b.nz = d->grid_dims[2];
+  }
+  if (list && V > INT32_MAX) return fail(MACH_ERR_UNSUPPORTED);
+  int tile[3];
+  pick_tile(per_cta, b.nx, b.ny, b.nz, list, tile);
+  b.tile_x = tile[0];
+  b.tile_y = tile[1];
+  b.tile_z = tile[2];
+  b.tiles_x = (b.nx + tile[0] - 1) / tile[0];
+  b.tiles_y = (b.ny + tile[1] - 1) / tile[1];
+  b.tiles_z = (b.nz + tile[2] - 1) / tile[2];
+  if (static_cast<int64_t>(b.tiles_x) * b.tiles_y * b.tiles_z > INT32_MAX) return fail(MACH_ERR_UNSUPPORTED);
+  b.apod = d->apod;
+  b.two_f = static_cast<float>(2.0 * d->f_number);
+  b.f_num = static_cast<float>(d->f_number);
+  b.s_max = static_cast<float>(S - 1);
+  b.r_f = static_cast<float>(d->fc / d->fs);
+  b.phase_R = fixed_cycles(d->fc / d->fs);
+  b.phase_Phi = fixed_cycles(d->fc * d->t0);
+  b.frame_tiles = frame_tiles;
+  *out = p;
+  return MACH_OK;
+}
+
+mach_status mach_plan_destroy(mach_plan p) {
+  if (!p) return MACH_OK;
+  release(p);
+  return MACH_OK;
+}
+
+static mach_status run(mach_plan p, const void* iq, float* pd, void* y, void* stream) {
+  if (!p || !iq || (!pd && !y)) return MACH_ERR_INVALID_ARG;
+  DasParams q = p->base;
+  q.iq = iq;
+  q.y = static_cast<float2*>(y);
+  q.pd = pd;
+  const cudaError_t e = launch_das(q, p->variant, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? MACH_OK : MACH_ERR_CUDA;
+}
+
+mach_status mach_das_run(mach_plan p, const void* iq_dev, void* y_dev, void* stream) {
+  if (!y_dev) return MACH_ERR_INVALID_ARG;
+  return run(p, iq_dev, nullptr, y_dev, stream);
+}
+
+mach_status mach_power_doppler(mach_plan p, const void* iq_dev, float* pd_dev, void* y_dev_or_null,
+                               void* stream) {
+  if (!pd_dev) return MACH_ERR_INVALID_ARG;
+  return run(p, iq_dev, pd_dev, y_dev_or_null, stream);
+}
+
+mach_status mach_plan_get_info(mach_plan p, mach_plan_info* info) {
+  if (!p || !info) return MACH_ERR_INVALID_ARG;
+  std::memset(info, 0, sizeof(*info));
+  const VariantShape& s = variant_shape(p->variant);
+  std::strncpy(info->variant, s.name, sizeof(info->variant) - 1);
+  info->frames_per_lane = s.frames_per_lane;
+  info->lanes_per_voxel = s.lanes_per_voxel;
+  info->voxels_per_cta = s.voxels_per_warp * s.warps;
+  info->threads_per_cta = s.warps * 32;
+  info->tile[0] = p->base.tile_x;
+  info->tile[1] = p->base.tile_y;
+  info->tile[2] = p->base.tile_z;
+  info->frame_tiles = p->base.frame_tiles;
+  info->ctas = static_cast<int64_t>(p->base.tiles_x) * p->base.tiles_y * p->base.tiles_z * p->base.frame_tiles;
+  info->smem_bytes = static_cast<int64_t>(das_smem_bytes(p->variant));
+  info->device_bytes = p->device_bytes;
+  return MACH_OK;
+}
+
+mach_status mach_plan_tx_table(mach_plan p, float* out_dev, void* stream) {
+  if (!p || !out_dev) return MACH_ERR_INVALID_ARG;
+  const size_t bytes = sizeof(float) * static_cast<size_t>(p->base.T) * p->base.V;
+  return cudaMemcpyAsync(out_dev, p->d_tx, bytes, cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? MACH_OK
+             : MACH_ERR_CUDA;
+}
+
+mach_status mach_das_terms(mach_plan p, const int64_t* vox_idx_dev, int64_t n, int32_t* i0_dev, float* w_dev,
+                           float* cw_dev, void* stream) {
+  if (!p || n < 0 || (n > 0 && !vox_idx_dev)) return MACH_ERR_INVALID_ARG;
+  return launch_terms(p->base, vox_idx_dev, n, i0_dev, w_dev, cw_dev, static_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? MACH_OK
+             : MACH_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+"""The C ABI without a GPU: the library loads, exports every declared entry point, and
+rejects bad arguments before touching CUDA."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2604_06257_gb300 as m
+from paper_2604_06257_gb300 import build as pkg_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pkg_build.build()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "mach.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mach_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported():
+    L = m.lib()
+    names = declared_functions()
+    assert "mach_das_plan" in names and "mach_power_doppler" in names
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(m.EXPORTS) >= set(names)
+
+
+def test_status_strings_and_version():
+    assert m.mach_status_string(0) == "ok"
+    assert "invalid" in m.mach_status_string(1)
+    assert m.mach_status_string(99) == "unknown status"
+    assert "sm_103a" in m.mach_version()
+
+
+def good_kwargs(**over):
+    kw = dict(ndim=2, elem_pos=np.stack([np.linspace(-1e-3, 1e-3, 8), np.zeros(8), np.zeros(8)], 1),
+              tx_angles=np.zeros((1, 2)), fs=20e6, fc=5e6, c=1540.0, n_samples=64, n_frames=4,
+              grid_dims=(4, 1, 4), grid_origin=(0.0, 0.0, 1e-3), grid_step=(1e-4, 0.0, 1e-4))
+    kw.update(over)
+    return kw
+
+
+BAD = [
+    dict(ndim=4),
+    dict(fs=0.0),
+    dict(fs=float("nan")),
+    dict(c=-1.0),
+    dict(fc=-1.0),
+    dict(f_number=-0.5),
+    dict(apod=7),
+    dict(iq_dtype=5),
+    dict(n_samples=1),
+    dict(n_samples=(1 << 24) + 1),
+    dict(n_frames=0),
+    dict(grid_dims=(0, 1, 4)),
+    dict(grid_dims=(4, 2, 4)),                       # 2D grid must have ny = 1
+    dict(grid_origin=(0.0, 1e-3, 1e-3)),             # 2D grid must lie in y = 0
+    dict(tx_angles=np.array([[0.0, 0.1]])),          # 2D: no elevation tilt
+    dict(elem_pos=np.ones((8, 3))),                  # 2D: elements at y = 0
+    dict(elem_pos=np.full((2, 3), np.inf)),
+    dict(grid_dims=None, vox_pos=np.zeros((0, 3))),
+    dict(grid_dims=None, vox_pos=np.array([[0.0, 1e-3, 1e-3]])),
+]
+
+
+@pytest.mark.parametrize("over", BAD)
+def test_invalid_descriptors_rejected_before_cuda(over):
+    kw = good_kwargs(**over)
+    if kw.get("grid_dims") is None:
+        kw.pop("grid_dims"); kw.pop("grid_origin"); kw.pop("grid_step")
+    d, keep = m.make_desc(**kw)
+    h = C.c_void_p(1234)
+    st = m.lib().mach_das_plan(C.byref(d), None, C.byref(h))
+    assert st == m.MACH_ERR_INVALID_ARG
+    assert h.value is None
+
+
+def test_null_arguments():
+    L = m.lib()
+    h = C.c_void_p()
+    assert L.mach_das_plan(None, None, C.byref(h)) == m.MACH_ERR_INVALID_ARG
+    d, keep = m.make_desc(**good_kwargs())
+    assert L.mach_das_plan(C.byref(d), None, None) == m.MACH_ERR_INVALID_ARG
+    assert L.mach_das_run(None, None, None, None) == m.MACH_ERR_INVALID_ARG
+    assert L.mach_power_doppler(None, None, None, None, None) == m.MACH_ERR_INVALID_ARG
+    assert L.mach_plan_destroy(None) == m.MACH_OK
+    assert L.mach_plan_get_info(None, None) == m.MACH_ERR_INVALID_ARG
+    assert L.mach_plan_tx_table(None, None, None) == m.MACH_ERR_INVALID_ARG
+    assert L.mach_das_terms(None, None, 0, None, None, None, None) == m.MACH_ERR_INVALID_ARG
+
+
+def test_unsupported_slab_size():
+    d, keep = m.make_desc(**good_kwargs(n_samples=1 << 24, n_frames=256))
+    h = C.c_void_p()
+    assert m.lib().mach_das_plan(C.byref(d), None, C.byref(h)) == m.MACH_ERR_UNSUPPORTED
+
+
+def test_valid_descriptor_without_gpu_reports_cuda_error():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    d, keep = m.make_desc(**good_kwargs())
+    h = C.c_void_p()
+    assert m.lib().mach_das_plan(C.byref(d), None, C.byref(h)) == m.MACH_ERR_CUDA
+    assert h.value is None

@@ -1,0 +1,335 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars (reading R9): integer sample indices and interpolation weights bit-exact against
+the oracle's float32 "contract" delays; complex frames (B-mode) NRMSE <= -100 dB and
+Power Doppler NRMSE <= -60 dB for complex64 IQ; with float16 IQ storage, <= -100 dB
+against the oracle run on the same (dequantised) samples and <= -60 dB against the
+oracle on the unquantised complex64 samples.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import paper_2604_06257_gb300 as m
+from paper_2604_06257_gb300 import build as pkg_build
+from metrics import nrmse_db, peak_db
+
+pytestmark = pytest.mark.gpu
+
+FP32_BMODE_DB = -100.0
+PD_DB = -60.0
+FP16_DB = -60.0
+# |y|^2 doubles the relative amplitude error of the stored samples: +6 dB over FP16_DB
+FP16_PD_DB = FP16_DB + 6.0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pkg_build.build()
+    m.lib()
+
+
+def plan_for(acq, **kw):
+    return m.Plan(**{**m.plan_kwargs(acq), **kw})
+
+
+def dev_iq(acq, iq):
+    """Device IQ in the acquisition's storage type."""
+    iq = iq.cuda()
+    if acq.iq_dtype == "f16x2":
+        return synth.iqmod.to_f16x2(iq)
+    return iq.contiguous()
+
+
+def check_terms(acq, plan, idx):
+    i0, w, cw = plan.terms(idx)
+    i0, w, cw = i0.cpu().numpy(), w.cpu().numpy(), cw.cpu().numpy()
+    tr = oracle.terms(acq, idx, mode="contract")
+    ref_i0 = np.where(tr["valid"], tr["i0"], -1)
+    np.testing.assert_array_equal(i0, ref_i0)
+    v = tr["valid"]
+    assert np.array_equal(w[v], tr["w"][v].astype(np.float32))       # exact value
+    assert np.max(np.abs(cw[v] - tr["cw"][v]), initial=0.0) < 2e-6
+    return int(v.sum())
+
+
+# ------------------------------------------------------------------ tables ----
+
+@pytest.mark.parametrize("name", ["bmode2d", "doppler2d", "volume3d"])
+@pytest.mark.parametrize("scale", ["small", "full"])
+def test_tx_table_bit_identical(name, scale):
+    acq = synth.make_acquisition(name, scale)
+    with plan_for(acq) as p:
+        got = p.tx_table().cpu().numpy()
+    ref = oracle.tx_table(acq)
+    assert got.shape == ref.shape
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+
+
+def test_tx_table_voxel_list_and_user_arrivals():
+    acq = synth.make_acquisition("volume3d", "small")
+    rng = np.random.default_rng(0)
+    P = acq.voxel_positions()[rng.permutation(acq.n_vox)[:500]].astype(np.float32)
+    lst = acq.replace(grid_dims=None, vox_pos=P)
+    with plan_for(lst) as p:
+        got = p.tx_table().cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), oracle.tx_table(lst).view(np.uint32))
+    # user-supplied arrival times in seconds (e.g. from a simulator)
+    arr = (rng.uniform(5e-6, 20e-6, (3, lst.n_vox))).astype(np.float32)
+    a3 = lst.replace(tx_angles=np.zeros((3, 2)))
+    with plan_for(a3, tx_table_dev=torch.from_numpy(arr).cuda(), tx_angles=None) as p:
+        got = p.tx_table().cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), oracle.tx_table(a3, tx_arrival=arr).view(np.uint32))
+
+
+# ------------------------------------------------------------ index terms ----
+
+@pytest.mark.parametrize("name", ["bmode2d", "doppler2d", "volume3d"])
+def test_terms_bit_exact_small(name):
+    acq = synth.make_acquisition(name, "small")
+    with plan_for(acq) as p:
+        n = check_terms(acq, p, np.arange(acq.n_vox))
+    assert n > 0
+
+
+@pytest.mark.parametrize("name", ["bmode2d", "doppler2d", "volume3d"])
+def test_terms_bit_exact_full_sampled(name):
+    acq = synth.make_acquisition(name, "full")
+    idx = np.sort(np.random.default_rng(11).choice(acq.n_vox, 1500, replace=False))
+    with plan_for(acq) as p:
+        assert check_terms(acq, p, idx) > 0
+
+
+@pytest.mark.parametrize("apod", ["none", "boxcar", "hann", "gauss"])
+def test_terms_all_windows_and_t0(apod):
+    acq = synth.make_acquisition("volume3d", "small").replace(apod=apod, t0=0.37e-6, f_number=1.3)
+    with plan_for(acq) as p:
+        check_terms(acq, p, np.arange(0, acq.n_vox, 3))
+
+
+# ------------------------------------------------------- beamformed output ----
+
+def compare(acq, iq_host, y, pd, idx=None, bmode_db=FP32_BMODE_DB, iq_oracle=None, pd_db=PD_DB):
+    y_ref, pd_ref = oracle.das(acq, iq_host if iq_oracle is None else iq_oracle, idx)
+    out = {}
+    if y is not None:
+        yk = y.cpu().numpy()
+        if idx is not None:
+            yk = yk[idx]
+        out["bmode_db"] = nrmse_db(yk, y_ref)
+        out["bmode_peak_db"] = peak_db(yk, y_ref)
+        assert out["bmode_db"] <= bmode_db, out
+    if pd is not None:
+        pk = pd.cpu().numpy().astype(np.float64)
+        if idx is not None:
+            pk = pk[idx]
+        out["pd_db"] = nrmse_db(pk, pd_ref)
+        out["pd_peak_db"] = peak_db(pk, pd_ref, power=True)
+        assert out["pd_db"] <= pd_db, out
+    return out
+
+
+@pytest.mark.parametrize("name", ["bmode2d", "doppler2d", "volume3d"])
+def test_das_and_pd_small(name):
+    acq, iq = synth.make(name, "small", device="cuda")
+    with plan_for(acq) as p:
+        y = p.run(iq)
+        pd, y2 = p.power_doppler(iq, want_y=True)
+        torch.cuda.synchronize()
+    assert torch.equal(y, y2)
+    r = compare(acq, iq.cpu(), y, pd)
+    print(name, r)
+
+
+def test_bmode2d_full_all_voxels():
+    acq, iq = synth.make("bmode2d", "full", device="cuda")
+    with plan_for(acq) as p:
+        y = p.run(iq)
+    print(compare(acq, iq.cpu(), y, None))
+
+
+def test_doppler2d_full_all_voxels():
+    """The benchmark workload, in the launch configuration the benchmark times."""
+    acq, iq = synth.make("doppler2d", "full", device="cuda")
+    with plan_for(acq) as p:
+        assert p.info()["variant"] == "frames_c64_ft32"
+        pd, y = p.power_doppler(iq, want_y=True)
+    print(compare(acq, iq.cpu(), y, pd))
+
+
+@pytest.mark.parametrize("iq_dtype", ["c64", "f16x2"])
+def test_volume3d_full_sampled(iq_dtype):
+    acq, iq = synth.make("volume3d", "full", device="cuda", iq_dtype=iq_dtype)
+    rng = np.random.default_rng(5)
+    idx = np.sort(rng.choice(acq.n_vox, 384, replace=False))
+    with plan_for(acq) as p:
+        diq = dev_iq(acq, iq)
+        pd, y = p.power_doppler(diq, want_y=True)
+        torch.cuda.synchronize()
+    if iq_dtype == "c64":
+        print(compare(acq, iq.cpu(), y, pd, idx))
+    else:
+        q = synth.iqmod.from_f16x2(diq.cpu())
+        print("vs dequantised", compare(acq, q, y, pd, idx))
+        print("vs complex64", compare(acq, iq.cpu(), y, pd, idx, bmode_db=FP16_DB, pd_db=FP16_PD_DB))
+    del iq
+
+
+@pytest.mark.parametrize("name", ["doppler2d", "volume3d"])
+def test_fp16_storage_small(name):
+    acq, iq = synth.make(name, "small", device="cuda", iq_dtype="f16x2")
+    diq = dev_iq(acq, iq)
+    with plan_for(acq) as p:
+        pd, y = p.power_doppler(diq, want_y=True)
+    q = synth.iqmod.from_f16x2(diq.cpu())
+    print(compare(acq, q, y, pd))
+    print(compare(acq, iq.cpu(), y, pd, bmode_db=FP16_DB, pd_db=FP16_PD_DB))
+
+
+# ------------------------------------------------------------- edge cases ----
+
+def small_random(F, C=9, T=2, S=300, iq_dtype="c64", grid=(13, 1, 11), apod="hann", **kw):
+    base = synth.doppler2d(nx=grid[0], nz=grid[2], n_frames=F, n_elem=C, n_samples=S,
+                           iq_dtype=iq_dtype).replace(
+        grid_origin=(-0.6e-3, 0.0, 4e-3), tx_angles=np.stack([np.linspace(-0.1, 0.1, T), np.zeros(T)], 1),
+        apod=apod, **kw)
+    return base
+
+
+@pytest.mark.parametrize("F", [1, 2, 3, 4, 5, 7, 16, 17, 32, 33, 64, 65, 130])
+def test_frame_counts_c64(F):
+    acq = small_random(F)
+    iq = synth.random_iq(acq, F, device="cuda")
+    with plan_for(acq) as p:
+        pd, y = p.power_doppler(iq, want_y=True)
+        info = p.info()
+    print(F, info["variant"], info["frame_tiles"], compare(acq, iq.cpu(), y, pd))
+
+
+@pytest.mark.parametrize("F", [1, 4, 6, 8, 12, 32, 36, 64, 68, 132])
+def test_frame_counts_f16(F):
+    acq = small_random(F, iq_dtype="f16x2")
+    iq = synth.random_iq(acq, 100 + F, device="cuda")
+    diq = dev_iq(acq, iq)
+    with plan_for(acq) as p:
+        pd, y = p.power_doppler(diq, want_y=True)
+    compare(acq, synth.iqmod.from_f16x2(diq.cpu()), y, pd)
+
+
+@pytest.mark.parametrize("C,T", [(1, 1), (3, 9), (17, 11), (33, 1)])
+def test_channel_and_transmit_counts(C, T):
+    for F in (3, 32, 64):
+        acq = small_random(F, C=C, T=T)
+        iq = synth.random_iq(acq, C * T + F, device="cuda")
+        with plan_for(acq) as p:
+            pd, y = p.power_doppler(iq, want_y=True)
+        compare(acq, iq.cpu(), y, pd)
+
+
+@pytest.mark.parametrize("apod", ["none", "boxcar", "gauss"])
+def test_windows_end_to_end(apod):
+    acq = small_random(32, apod=apod, t0=-0.2e-6)
+    iq = synth.random_iq(acq, 7, device="cuda")
+    with plan_for(acq) as p:
+        y = p.run(iq)
+    compare(acq, iq.cpu(), y, None)
+
+
+def test_voxel_list_any_order_3d():
+    acq = synth.make_acquisition("volume3d", "small").replace(n_frames=32)
+    rng = np.random.default_rng(3)
+    P = acq.voxel_positions()[rng.permutation(acq.n_vox)[:777]].astype(np.float32)
+    lst = acq.replace(grid_dims=None, vox_pos=P)
+    iq = synth.random_iq(lst, 8, device="cuda")
+    with plan_for(lst) as p:
+        pd, y = p.power_doppler(iq, want_y=True)
+    compare(lst, iq.cpu(), y, pd)
+
+
+def test_minimal_and_degenerate():
+    # two samples per channel, one element, one voxel
+    acq = synth.doppler2d(nx=1, nz=1, n_frames=1, n_elem=1, n_samples=2).replace(
+        grid_origin=(0.0, 0.0, 0.5 * 1540 / 20.8e6 / 2), apod="none")
+    iq = synth.random_iq(acq, 1, device="cuda")
+    with plan_for(acq) as p:
+        y = p.run(iq)
+    y_ref, _ = oracle.das(acq, iq.cpu())
+    assert abs(y.cpu().numpy()[0, 0] - y_ref[0, 0]) < 1e-5 * max(1.0, abs(y_ref[0, 0]))
+    # every term past the end: exact zeros
+    late = small_random(32, t0=-1e-3)
+    iq = synth.random_iq(late, 2, device="cuda")
+    with plan_for(late) as p:
+        pd, y = p.power_doppler(iq, want_y=True)
+    assert torch.count_nonzero(y).item() == 0 and torch.count_nonzero(pd).item() == 0
+
+
+def test_large_sample_count():
+    """S near the float-exact index limit region (2^20 samples)."""
+    acq = small_random(2, C=2, T=1, S=1 << 20).replace(t0=-0.9 * (1 << 20) / 20.8e6)
+    iq = synth.random_iq(acq, 3, device="cuda")
+    with plan_for(acq) as p:
+        y = p.run(iq)
+        check_terms(acq, p, np.arange(acq.n_vox))
+    compare(acq, iq.cpu(), y, None)
+
+
+# --------------------------------------------------------- streams, graphs ----
+
+def test_non_default_stream_and_graph_capture():
+    acq, iq = synth.make("doppler2d", "small", device="cuda")
+    with plan_for(acq) as p:
+        ref_pd, ref_y = p.power_doppler(iq, want_y=True)
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream()
+        pd = torch.empty_like(ref_pd)
+        y = torch.empty_like(ref_y)
+        with torch.cuda.stream(s):
+            m.mach_power_doppler(p.handle, iq, pd, y, stream=s)
+        s.synchronize()
+        assert torch.equal(pd, ref_pd) and torch.equal(y, ref_y)
+        g = torch.cuda.CUDAGraph()
+        pd2 = torch.zeros_like(ref_pd)
+        y2 = torch.zeros_like(ref_y)
+        with torch.cuda.graph(g):
+            m.mach_power_doppler(p.handle, iq, pd2, y2)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(pd2, ref_pd) and torch.equal(y2, ref_y)
+
+
+def test_errors_leave_outputs_untouched():
+    acq, iq = synth.make("doppler2d", "small", device="cuda")
+    with plan_for(acq) as p:
+        y = torch.full((acq.n_vox, acq.n_frames), 7.0 + 0j, dtype=torch.complex64, device="cuda")
+        import ctypes as C
+        st = m.lib().mach_power_doppler(p.handle, iq.data_ptr(), None, y.data_ptr(), None)
+        assert st == m.MACH_ERR_INVALID_ARG
+        st = m.lib().mach_das_run(p.handle, None, y.data_ptr(), None)
+        assert st == m.MACH_ERR_INVALID_ARG
+        torch.cuda.synchronize()
+        assert torch.all(y == 7.0)
+
+
+def test_injected_allocation_failure_and_no_leak():
+    acq = synth.make_acquisition("volume3d", "small").replace(n_frames=130)   # frame tiles -> 4 allocations
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for k in (1, 2, 3, 4):
+        m.mach_debug_fail_alloc_after(k)
+        with pytest.raises(m.MachError) as e:
+            plan_for(acq)
+        assert e.value.status == m.MACH_ERR_OOM
+    m.mach_debug_fail_alloc_after(0)
+    with plan_for(acq) as p:
+        assert p.info()["frame_tiles"] > 1
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < (64 << 20)
+
+
+def test_oversize_plan_is_refused_before_allocating():
+    acq = synth.doppler2d(nx=1 << 15, nz=1 << 15, n_frames=32)
+    with pytest.raises(m.MachError) as e:
+        plan_for(acq.replace(tx_angles=np.zeros((512, 2))))
+    assert e.value.status == m.MACH_ERR_OOM
