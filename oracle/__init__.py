@@ -42,20 +42,23 @@ class _Desc(C.Structure):
 _lib = None
 
 
+def configure(L):
+    """Declare the C signatures on a loaded oracle library (returns it)."""
+    vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int
+    L.oracle_das.argtypes = [C.POINTER(_Desc), vp, vp, i64, vp, vp, i32]
+    L.oracle_terms.argtypes = [C.POINTER(_Desc), vp, i64, vp, vp, vp, vp, vp, vp, i32]
+    L.oracle_tx_table.argtypes = [C.POINTER(_Desc), vp]
+    L.oracle_tx_exact.argtypes = [C.POINTER(_Desc), vp, i64, vp]
+    L.oracle_max_threads.restype = C.c_int
+    for f in (L.oracle_das, L.oracle_terms, L.oracle_tx_table, L.oracle_tx_exact):
+        f.restype = C.c_int
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = C.CDLL(path)
-        vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int
-        L.oracle_das.argtypes = [C.POINTER(_Desc), vp, vp, i64, vp, vp, i32]
-        L.oracle_terms.argtypes = [C.POINTER(_Desc), vp, i64, vp, vp, vp, vp, vp, vp, i32]
-        L.oracle_tx_table.argtypes = [C.POINTER(_Desc), vp]
-        L.oracle_tx_exact.argtypes = [C.POINTER(_Desc), vp, i64, vp]
-        L.oracle_max_threads.restype = C.c_int
-        for f in (L.oracle_das, L.oracle_terms, L.oracle_tx_table, L.oracle_tx_exact):
-            f.restype = C.c_int
-        _lib = L
+        _lib = configure(C.CDLL(_build.build()))
     return _lib
 
 
