@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "DAS points/s (voxel x channel x transmit x frame, Eq. 1)"
 UNIT = "points/s"
 PAPER_POINTS_PER_S = 258_052_096 / 0.23e-3      # Sec. 4.2: 0.23 ms on an RTX 5090, 251^2 px
-KERNEL_SOURCES = ("k_das.cu", "das_term.cuh", "mach_internal.h")
+KERNEL_SOURCES = ("k_das.cu", "k_das_staged.cu", "das_term.cuh", "async_copy.cuh", "mach_internal.h")
 FLUSH_BYTES = 256 << 20                           # > 129 MB L2
 
 
@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", default="", help="force a kernel variant (ablations)")
+    ap.add_argument("--iq-dtype", default="c64", choices=["c64", "f16x2"])
     return ap.parse_args()
 
 
@@ -141,11 +143,17 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+DESCRIBE = {"doppler2d": "rotating-disk Doppler stand-in (Sec. 4.1 shape)",
+            "volume3d": "32x32 matrix-array volume (Sec. 6 shape)",
+            "bmode2d": "steered plane-wave B-mode (Sec. 2.1 compounding)"}
+
+
 def workload_config(acq, extra=None):
-    d = {"workload": f"{acq.name}: rotating-disk Doppler stand-in (Sec. 4.1 shape), "
-                     f"{acq.grid_dims[0]}x{acq.grid_dims[2]} px, {acq.n_elem} ch, {acq.n_tx} tx, "
-                     f"{acq.n_frames} frames, {acq.n_samples} samples, {acq.iq_dtype} IQ, "
-                     f"F# {acq.f_number} {acq.apod}; outputs B-mode frames + Power Doppler",
+    kind = acq.name.split("_")[0]
+    grid = "x".join(str(n) for n in acq.grid_dims if n > 1)
+    d = {"workload": f"{acq.name}: {DESCRIBE.get(kind, kind)}, {grid} voxels, {acq.n_elem} ch, "
+                     f"{acq.n_tx} tx, {acq.n_frames} frames, {acq.n_samples} samples, {acq.iq_dtype} IQ, "
+                     f"F# {acq.f_number} {acq.apod}; outputs complex frames + Power Doppler",
          "voxels": acq.n_vox, "channels": acq.n_elem, "transmits": acq.n_tx,
          "frames": acq.n_frames, "samples": acq.n_samples,
          "points_per_step": acq.points,
@@ -156,22 +164,36 @@ def workload_config(acq, extra=None):
 
 
 def oracle_sample(acq, iq_host, seconds, min_vox=64):
-    """Time the oracle on an evenly strided voxel sample sized to ~``seconds``."""
+    """Time the oracle on a bounded sample of the workload: the whole workload repeated
+    until about ``seconds`` of work if one pass is shorter, else an evenly strided voxel
+    subset sized to about ``seconds``."""
     import numpy as np
     import oracle
     cal = np.arange(0, acq.n_vox, max(1, acq.n_vox // 512))[:512]
     t = time.perf_counter()
     oracle.das(acq, iq_host, cal, want_y=False)
     dt = max(time.perf_counter() - t, 1e-6)
+    full_est = dt * acq.n_vox / len(cal)
+    if full_est < seconds:
+        reps, done, t0 = 0, 0.0, time.perf_counter()
+        while done < seconds:
+            oracle.das(acq, iq_host, None, want_y=True)
+            reps += 1
+            done = time.perf_counter() - t0
+        pts = acq.points * reps
+        sample = (f"the whole workload ({acq.n_vox} voxels, all channels, transmits and frames), "
+                  f"{reps} passes in {done:.1f} s, FP64")
+        return {"value": pts / done, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                "sample": sample}
     n = int(min(acq.n_vox, max(min_vox, len(cal) * seconds / dt)))
     idx = np.linspace(0, acq.n_vox - 1, n).astype(np.int64)
     t = time.perf_counter()
-    oracle.das(acq, iq_host, idx, want_y=False)
+    oracle.das(acq, iq_host, idx, want_y=True)
     dt = time.perf_counter() - t
     pts = n * acq.n_elem * acq.n_tx * acq.n_frames
     return {"value": pts / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
             "sample": f"{n} of {acq.n_vox} voxels (evenly strided), all channels, transmits "
-                      f"and frames; one call, {dt:.2f} s, FP64"}
+                      f"and frames; one pass, {dt:.2f} s, FP64"}
 
 
 # ---------------------------------------------------------------- our arm ----
@@ -191,8 +213,14 @@ def run_ours(args):
     pkg_build.build()
     m.lib()
 
-    acq, iq = synth.make(args.workload, "full", device=dev, seed=synth.SEEDS[args.workload] + rank)
+    acq, iq = synth.make(args.workload, "full", device=dev, seed=synth.SEEDS[args.workload] + rank,
+                         iq_dtype=args.iq_dtype)
+    if args.iq_dtype == "f16x2":
+        iq = synth.iqmod.to_f16x2(iq)
+    if args.variant:
+        m.mach_debug_force_variant(args.variant)
     plan = m.Plan(**m.plan_kwargs(acq))
+    m.mach_debug_force_variant(None)
     info = plan.info()
     V, F = acq.n_vox, acq.n_frames
     pd = torch.empty(V, dtype=torch.float32, device=dev)
@@ -245,7 +273,8 @@ def run_ours(args):
     fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12                     # TFLOP/s
     flops = active_points * 16.0                                            # 8 FMA per term-frame
     achieved = flops / t_launch / 1e12
-    comp = counts.compulsory_bytes(V, acq.n_elem, acq.n_tx, acq.n_samples, F, write_y=True, write_pd=True)
+    comp = counts.compulsory_bytes(V, acq.n_elem, acq.n_tx, acq.n_samples, F, write_y=True, write_pd=True,
+                                   iq_bytes=4 if args.iq_dtype == "f16x2" else 8)
     traffic = profiled_traffic(info["variant"], acq.name)
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": traffic,
@@ -256,8 +285,8 @@ def run_ours(args):
                            f"and in range: {active_terms} of {V * acq.n_elem * acq.n_tx} terms",
             "hbm": {"compulsory_bytes": comp, "achieved_gbs": comp / t_launch / 1e9,
                     "peak_gbs": hbm_peak, "frac": comp / t_launch / 1e9 / hbm_peak},
-            "sm_load_path": {"bytes_per_term_frame": 16,
-                             "achieved_gbs": active_points * 16 / t_launch / 1e9}}
+            "sm_load_path": {"bytes_per_term_frame": 16 if args.iq_dtype == "c64" else 8,
+                             "achieved_gbs": active_points * (16 if args.iq_dtype == "c64" else 8) / t_launch / 1e9}}
 
     # end to end through the public API with host buffers (pinned), copies timed
     e2e = None
@@ -285,11 +314,11 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32", "data": "synthetic",
+                "dtype": "f32" if args.iq_dtype == "c64" else "f32 (f16 IQ storage)", "data": "synthetic",
                 "config": workload_config(acq, {"parallelism": f"replicas{world}",
                                                 "kernel_variant": info["variant"],
                                                 "active_fraction": active_terms / (V * acq.n_elem * acq.n_tx)}),
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "plan": info,
                 "gpu_launches": launches_per_step * args.steps,
                 "clocks": clk, "wall_s_timed_region": t_wall,
                 "paper_context": {"points_per_s": PAPER_POINTS_PER_S,

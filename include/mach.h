@@ -140,6 +140,10 @@ typedef struct {
     int64_t ctas;            /* blocks of one run                                      */
     int64_t smem_bytes;      /* dynamic shared memory per block                        */
     int64_t device_bytes;    /* device memory held by the plan                         */
+    int32_t ring_rows;       /* staged variants: sample rows per shared-memory slot     */
+    int32_t ring_slots;      /* staged variants: slots in the ring (0 otherwise)        */
+    int64_t copy_pairs;      /* staged variants: (tile, transmit, element) windows one
+                                run copies; pairs no voxel can use are skipped          */
 } mach_plan_info;
 
 mach_status mach_plan_get_info(mach_plan p, mach_plan_info *info);
@@ -155,12 +159,30 @@ mach_status mach_plan_tx_table(mach_plan p, float *out_dev, void *stream);
 mach_status mach_das_terms(mach_plan p, const int64_t *vox_idx_dev, int64_t n,
                            int32_t *i0_dev, float *w_dev, float *cw_dev, void *stream);
 
+/* Synchronise `stream`, then report and clear the plan's device error word:
+ * MACH_OK, or MACH_ERR_TIMEOUT when a bounded device-side wait of an earlier run on
+ * this plan gave up (that run's outputs are then incomplete).  The staged kernels wait
+ * on shared-memory barriers for their bulk copies; each wait polls a bounded number of
+ * times (about a second) and then abandons the block instead of hanging the device. */
+mach_status mach_plan_device_status(mach_plan p, void *stream);
+
 /* Library version string, e.g. "mach-gb300 0.1.0 sm_103a". */
 const char *mach_version(void);
 
 /* Test hook: make the n-th device allocation from now fail (n >= 1); n <= 0 disarms.
  * Lets tests exercise the MACH_ERR_OOM clean-up path without exhausting memory. */
 void mach_debug_fail_alloc_after(int32_t n);
+
+/* Test hooks (process-wide, not thread-safe; read when a plan is created):
+ *  - force the kernel variant named `name` (mach_plan_info.variant) for later plans, or
+ *    restore the automatic choice with NULL / "".  INVALID_ARG for an unknown name;
+ *    mach_das_plan returns UNSUPPORTED if the forced variant cannot serve the plan.
+ *  - set the polls per bounded device wait (0 restores the default).
+ *  - make the staged producer announce its copies without issuing them, so that the
+ *    consumers' waits run out (exercises MACH_ERR_TIMEOUT without a fault). */
+mach_status mach_debug_force_variant(const char *name);
+void mach_debug_set_wait_limit(uint32_t polls);
+void mach_debug_stall_producer(int32_t on);
 
 #ifdef __cplusplus
 }

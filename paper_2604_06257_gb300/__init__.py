@@ -28,7 +28,8 @@ IQ_DTYPE = {"c64": 0, "f16x2": 1}
 
 EXPORTS = ("mach_das_plan", "mach_das_run", "mach_power_doppler", "mach_plan_destroy",
            "mach_status_string", "mach_plan_get_info", "mach_plan_tx_table", "mach_das_terms",
-           "mach_version", "mach_debug_fail_alloc_after")
+           "mach_version", "mach_debug_fail_alloc_after", "mach_plan_device_status",
+           "mach_debug_force_variant", "mach_debug_set_wait_limit", "mach_debug_stall_producer")
 
 
 class MachError(RuntimeError):
@@ -54,7 +55,8 @@ class mach_plan_info(C.Structure):
         ("variant", C.c_char * 40), ("frames_per_lane", C.c_int32), ("lanes_per_voxel", C.c_int32),
         ("voxels_per_cta", C.c_int32), ("threads_per_cta", C.c_int32), ("tile", C.c_int32 * 3),
         ("frame_tiles", C.c_int32), ("ctas", C.c_int64), ("smem_bytes", C.c_int64),
-        ("device_bytes", C.c_int64),
+        ("device_bytes", C.c_int64), ("ring_rows", C.c_int32), ("ring_slots", C.c_int32),
+        ("copy_pairs", C.c_int64),
     ]
 
     def as_dict(self):
@@ -62,7 +64,8 @@ class mach_plan_info(C.Structure):
                 "lanes_per_voxel": self.lanes_per_voxel, "voxels_per_cta": self.voxels_per_cta,
                 "threads_per_cta": self.threads_per_cta, "tile": list(self.tile),
                 "frame_tiles": self.frame_tiles, "ctas": self.ctas, "smem_bytes": self.smem_bytes,
-                "device_bytes": self.device_bytes}
+                "device_bytes": self.device_bytes, "ring_rows": self.ring_rows,
+                "ring_slots": self.ring_slots, "copy_pairs": self.copy_pairs}
 
 
 _lib = None
@@ -89,6 +92,14 @@ def lib():
         L.mach_version.restype = C.c_char_p
         L.mach_debug_fail_alloc_after.argtypes = [i32]
         L.mach_debug_fail_alloc_after.restype = None
+        L.mach_plan_device_status.argtypes = [vp, vp]
+        L.mach_plan_device_status.restype = C.c_int
+        L.mach_debug_force_variant.argtypes = [C.c_char_p]
+        L.mach_debug_force_variant.restype = C.c_int
+        L.mach_debug_set_wait_limit.argtypes = [C.c_uint32]
+        L.mach_debug_set_wait_limit.restype = None
+        L.mach_debug_stall_producer.argtypes = [i32]
+        L.mach_debug_stall_producer.restype = None
         for f in ("mach_das_plan", "mach_das_run", "mach_power_doppler", "mach_plan_destroy",
                   "mach_plan_get_info", "mach_plan_tx_table", "mach_das_terms"):
             getattr(L, f).restype = C.c_int
@@ -108,6 +119,25 @@ def mach_version() -> str:
 
 def mach_debug_fail_alloc_after(n: int) -> None:
     lib().mach_debug_fail_alloc_after(int(n))
+
+
+def mach_debug_force_variant(name) -> None:
+    st = lib().mach_debug_force_variant(None if not name else name.encode())
+    if st != MACH_OK:
+        raise MachError(st, "mach_debug_force_variant")
+
+
+def mach_debug_set_wait_limit(polls: int) -> None:
+    lib().mach_debug_set_wait_limit(int(polls))
+
+
+def mach_debug_stall_producer(on: bool) -> None:
+    lib().mach_debug_stall_producer(1 if on else 0)
+
+
+def mach_plan_device_status(plan: int, stream=None) -> int:
+    """Synchronise and return the plan's device status code (MACH_OK or MACH_ERR_TIMEOUT)."""
+    return int(lib().mach_plan_device_status(plan, _stream_ptr(stream)))
 
 
 def _stream_ptr(stream):
@@ -261,6 +291,9 @@ class Plan:
     # geometry ----------------------------------------------------------------
     def info(self) -> dict:
         return mach_plan_get_info(self.handle)
+
+    def device_status(self, stream=None) -> int:
+        return mach_plan_device_status(self.handle, stream)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -89,4 +89,34 @@ __device__ __forceinline__ int64_t tile_voxel(const DasParams& p, int64_t tile, 
   return gx + static_cast<int64_t>(p.nx) * (gy + static_cast<int64_t>(p.ny) * gz);
 }
 
+// Sample rows [lo, lo + rows) of element e that the voxels of a tile can touch for one
+// transmit, from the tile's bounding box (sample units) and its transmit-delay range:
+// the receive delay over the box lies between the distances from e to the nearest and
+// farthest points of the box.  Returns false when no voxel of the tile can have a kept
+// term (aperture or range rule), so the pair is skipped.  Two rows of margin on each
+// side absorb float rounding of the bounds.
+__device__ __forceinline__ bool pair_window(const float4 blo, const float4 bhi, const float2 txr,
+                                            const float4 e, const DasParams& p, int& lo, int& rows) {
+  const float ax = blo.x - e.x, bx = bhi.x - e.x;
+  const float ay = blo.y - e.y, by = bhi.y - e.y;
+  const float az = blo.z - e.z, bz = bhi.z - e.z;
+  const float nx = fmaxf(fmaxf(ax, -bx), 0.f), ny = fmaxf(fmaxf(ay, -by), 0.f), nz = fmaxf(fmaxf(az, -bz), 0.f);
+  const float fx = fmaxf(fabsf(ax), fabsf(bx)), fy = fmaxf(fabsf(ay), fabsf(by)), fz = fmaxf(fabsf(az), fabsf(bz));
+  if (p.apod != MACH_APOD_NONE) {
+    const float rho_min = sqrtf(nx * nx + ny * ny);
+    if (!(bz > 0.f) || rho_min * p.two_f > bz * 1.00001f + 1e-3f) return false;
+  }
+  const float rmin = sqrtf(nx * nx + ny * ny + nz * nz);
+  const float rmax = sqrtf(fx * fx + fy * fy + fz * fz);
+  const float smin = txr.x + rmin, smax = txr.y + rmax;
+  if (!(smax >= -1.f) || !(smin < p.s_max + 1.f)) return false;
+  const float top = static_cast<float>(p.S);
+  const int l = max(0, static_cast<int>(floorf(fmaxf(smin, -8.f))) - 2);
+  const int h = min(p.S - 1, static_cast<int>(floorf(fminf(smax, top))) + 3);
+  if (h < l + 1) return false;
+  lo = l;
+  rows = h - l + 1;
+  return true;
+}
+
 }  // namespace mach

@@ -107,6 +107,10 @@ __global__ void __launch_bounds__(NWARP * 32) k_das_frames(const DasParams p) {
   const int64_t v_term = tile_voxel(p, tile, warp * WV + (lane % WV));
   const float4 vpos = v_term >= 0 ? p.vox[v_term] : make_float4(0.f, 0.f, 0.f, 0.f);
   const int c_sub = lane / WV;
+  // slot (g, k) of element sub-round j is stored at j*WV + k*G + g: the G groups of the
+  // warp then read G consecutive entries in one conflict-free broadcast
+  const int q_lane = lane % WV;
+  const int store_at = c_sub * WV + (q_lane % VPG) * G + (q_lane / VPG);
 
   float2 acc[VPG][FPL];
 #pragma unroll
@@ -127,7 +131,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_das_frames(const DasParams p) {
       for (int tt = 0; tt < tn; ++tt) {
         float4 r = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
         if (geo.a >= 0.f) r = term_record(__ldg(&p.tx[static_cast<size_t>(tb + tt) * p.V + v_term]), geo, p);
-        terms[tt * 32 + lane] = r;
+        terms[tt * 32 + store_at] = r;
       }
       __syncwarp();
       for (int tt = 0; tt < tn; ++tt) {
@@ -138,7 +142,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_das_frames(const DasParams p) {
           const IQ* base = iq + (static_cast<size_t>(tb + tt) * p.C + c2) * slab;
 #pragma unroll
           for (int k = 0; k < VPG; ++k) {
-            const float4 r = terms[tt * 32 + j * WV + g * VPG + k];
+            const float4 r = terms[tt * 32 + j * WV + k * G + g];
             const int i0 = __float_as_int(r.w);
             if (i0 >= 0) {
               const float c1r = r.x * r.z, c1i = r.y * r.z;
@@ -262,15 +266,21 @@ namespace {
 constexpr int kWarps = 8;
 //                          name                FPL  lanes vox/warp  FT  warps  ch-lanes
 const VariantShape kShapes[V_COUNT] = {
-    {"channels_c64_cl8", 1, 8, 4, 4, kWarps, true},
-    {"frames_c64_ft16", 2, 8, 32, 16, kWarps, false},
-    {"frames_c64_ft32", 4, 8, 32, 32, kWarps, false},
-    {"frames_c64_ft64", 4, 16, 16, 64, kWarps, false},
-    {"frames_c64_scalar_ft32", 1, 32, 16, 32, kWarps, false},
-    {"channels_f16_cl8", 1, 8, 4, 4, kWarps, true},
-    {"frames_f16_ft32", 4, 8, 32, 32, kWarps, false},
-    {"frames_f16_ft64", 4, 16, 16, 64, kWarps, false},
-    {"frames_f16_scalar_ft32", 1, 32, 16, 32, kWarps, false},
+    //  name                      FPL lanes vox/warp FT  warps ch-lanes staged ring bytes
+    {"channels_c64_cl8",           1,  8,   4,    4,  kWarps, true,  false, 0, 8},
+    {"frames_c64_ft16",            2,  8,  32,   16,  kWarps, false, false, 0, 8},
+    {"frames_c64_ft32",            4,  8,  32,   32,  kWarps, false, false, 0, 8},
+    {"frames_c64_ft64",            4, 16,  16,   64,  kWarps, false, false, 0, 8},
+    {"frames_c64_scalar_ft32",     1, 32,  16,   32,  kWarps, false, false, 0, 8},
+    {"channels_f16_cl8",           1,  8,   4,    4,  kWarps, true,  false, 0, 4},
+    {"frames_f16_ft32",            4,  8,  32,   32,  kWarps, false, false, 0, 4},
+    {"frames_f16_ft64",            4, 16,  16,   64,  kWarps, false, false, 0, 4},
+    {"frames_f16_scalar_ft32",     1, 32,  16,   32,  kWarps, false, false, 0, 4},
+    {"staged_c64_ft32",            4,  8,  32,   32,  kWarps, false, true,  4, 8},
+    {"staged_c64_ft64",            4, 16,  16,   64,  kWarps, false, true,  4, 8},
+    {"staged_f16_ft32",            4,  8,  32,   32,  kWarps, false, true,  4, 4},
+    {"staged_f16_ft64",            4, 16,  16,   64,  kWarps, false, true,  4, 4},
+    {"staged_c64_ft32_v4",         4,  8,  16,   32,  kWarps, false, true,  4, 8},
 };
 
 template <class K>
@@ -289,6 +299,7 @@ size_t das_smem_bytes(Variant v) {
 }
 
 cudaError_t launch_das(const DasParams& p, Variant v, cudaStream_t s) {
+  if (kShapes[v].staged) return launch_das_staged(p, v, s);
   const size_t sm = das_smem_bytes(v);
   cudaError_t e;
   switch (v) {

@@ -23,6 +23,11 @@ enum Variant : int32_t {
   V_F32_H16,         // frame lanes, 32-frame tile, float16 pairs (F % 4 == 0)
   V_F64_H16,         // frame lanes, 64-frame tile, float16 pairs (F % 4 == 0)
   V_S32_H16,         // frame lanes, 32-frame tile, scalar loads (any F)
+  V_ST32_C64,        // staged (bulk copies into shared memory), 32-frame tile, complex64
+  V_ST64_C64,        // staged, 64-frame tile, complex64
+  V_ST32_H16,        // staged, 32-frame tile, float16 pairs
+  V_ST64_H16,        // staged, 64-frame tile, float16 pairs
+  V_ST32_C64_V4,     // staged, 32-frame tile, 4 voxels per lane group (ablation)
   V_COUNT
 };
 
@@ -32,8 +37,11 @@ struct VariantShape {
   int lanes_per_voxel;   // frame lanes per voxel, or channel slices per voxel
   int voxels_per_warp;
   int frame_tile;        // frames covered by one block
-  int warps;             // warps per block
+  int warps;             // warps per block (consumer warps for staged variants)
   bool channel_lanes;
+  bool staged;           // + one producer warp and a shared-memory ring of sample windows
+  int ring_slots;
+  int iq_bytes;          // bytes per complex sample
 };
 
 const VariantShape& variant_shape(Variant v);
@@ -60,6 +68,13 @@ struct DasParams {
   uint32_t phase_R;     // round(2^32 frac(fc / fs))
   uint32_t phase_Phi;   // round(2^32 frac(fc t0))
   int frame_tiles;
+  // staged variants only
+  const float4* tbox;   // [tiles][2] voxel bounding box of each tile (sample units)
+  const float2* txr;    // [tiles][T] (min, max) transmit delay over each tile
+  int rows_cap;         // rows of one ring slot
+  uint32_t wait_limit;  // polls before a wait gives up
+  int* err;             // device error word (bit 0: a wait timed out)
+  int debug_stall;      // test hook: the producer announces copies but never issues them
 };
 
 // Tables built once per plan (kernel K1).
@@ -80,6 +95,12 @@ struct TableParams {
 
 cudaError_t launch_tables(const TableParams& tp, cudaStream_t s);
 cudaError_t launch_das(const DasParams& p, Variant v, cudaStream_t s);
+// Per-tile bounds for the staged variants; returns the largest window (rows) and the
+// number of (tile, transmit, element) triples that need a copy.
+cudaError_t launch_tile_bounds(const DasParams& p, float4* tbox, float2* txr, int* d_rows_pairs,
+                               cudaStream_t s);
+size_t staged_smem_bytes(Variant v, int rows_cap, int F);
+cudaError_t launch_das_staged(const DasParams& p, Variant v, cudaStream_t s);
 cudaError_t launch_terms(const DasParams& p, const int64_t* vox_idx, int64_t n, int32_t* i0,
                          float* w, float* cw, cudaStream_t s);
 size_t das_smem_bytes(Variant v);

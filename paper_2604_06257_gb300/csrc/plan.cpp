@@ -23,12 +23,22 @@ struct mach_plan_s {
   float4* d_elem = nullptr;
   float* d_tx = nullptr;
   float* d_pd_part = nullptr;
+  float4* d_tbox = nullptr;     // staged variants: per-tile bounding boxes
+  float2* d_txr = nullptr;      // staged variants: per-tile transmit-delay ranges
+  int* d_err = nullptr;         // device error word
+  int rows_cap = 0;
+  int64_t copy_pairs = 0;
   int64_t device_bytes = 0;
 };
 
 namespace {
 
 int g_fail_alloc_countdown = 0;   // test hook: > 0 -> the n-th allocation fails
+int g_force_variant = -1;         // test hook: variant index, or -1 for automatic choice
+uint32_t g_wait_limit = 0;        // test hook: polls per bounded wait (0 = default)
+int g_stall = 0;                  // test hook: staged producer never issues its copies
+constexpr uint32_t kDefaultWaitLimit = 1u << 24;   // ~ seconds of polling
+constexpr size_t kStagedSmemCap = 110 * 1024;       // leaves room for two blocks per SM
 
 mach_status dev_alloc(void** p, size_t bytes, int64_t* total) {
   *p = nullptr;
@@ -102,12 +112,43 @@ mach_status validate(const mach_das_desc* d) {
 Variant pick_variant(int iq_dtype, int F) {
   if (iq_dtype == MACH_IQ_C64) {
     if (F <= 4) return V_CH_C64;
-    if (F % 2 == 0) return F <= 16 ? V_F16_C64 : (F <= 32 ? V_F32_C64 : V_F64_C64);
+    if (F % 2 == 0) {
+      if (F <= 16) return V_F16_C64;
+      if (F <= 32) return V_ST32_C64;
+      if (F <= 64) return V_ST64_C64;
+      return V_F64_C64;
+    }
     return V_S32_C64;
   }
   if (F <= 4) return V_CH_H16;
-  if (F % 4 == 0) return F <= 32 ? V_F32_H16 : V_F64_H16;
+  if (F % 4 == 0) {
+    if (F <= 16) return V_F32_H16;
+    if (F <= 32) return V_ST32_H16;
+    if (F <= 64) return V_ST64_H16;
+    return V_F64_H16;
+  }
   return V_S32_H16;
+}
+
+// The non-staged variant with the same frame tile (used when the ring would not fit).
+Variant unstaged(Variant v) {
+  switch (v) {
+    case V_ST32_C64: case V_ST32_C64_V4: return V_F32_C64;
+    case V_ST64_C64: return V_F64_C64;
+    case V_ST32_H16: return V_F32_H16;
+    case V_ST64_H16: return V_F64_H16;
+    default: return v;
+  }
+}
+
+bool variant_accepts(Variant v, int iq_dtype, int F) {
+  const VariantShape& s = variant_shape(v);
+  if ((s.iq_bytes == 8) != (iq_dtype == MACH_IQ_C64)) return false;
+  if (s.channel_lanes) return F <= s.frame_tile;
+  const int vec = s.frames_per_lane == 1 ? 1 : (s.iq_bytes == 8 ? 2 : 4);
+  if (F % vec != 0) return false;
+  if (s.staged && F > s.frame_tile) return false;
+  return true;
 }
 
 // Voxel tile of one block: compact boxes so that the voxels sharing a block (and the
@@ -140,6 +181,9 @@ void release(mach_plan_s* p) {
   cudaFree(p->d_elem);
   cudaFree(p->d_tx);
   cudaFree(p->d_pd_part);
+  cudaFree(p->d_tbox);
+  cudaFree(p->d_txr);
+  cudaFree(p->d_err);
   delete p;
 }
 
@@ -163,6 +207,25 @@ const char* mach_version(void) { return "mach-gb300 0.1.0 sm_103a"; }
 
 void mach_debug_fail_alloc_after(int32_t n) { g_fail_alloc_countdown = n > 0 ? n : 0; }
 
+// Tile geometry of a variant: voxel box per block and the number of blocks.
+static mach_status configure_tiles(DasParams& b, Variant var, bool list, int64_t V, int F) {
+  const VariantShape& shp = variant_shape(var);
+  const int per_cta = shp.voxels_per_warp * shp.warps;
+  int tile[3];
+  pick_tile(per_cta, b.nx, b.ny, b.nz, list, tile);
+  b.tile_x = tile[0];
+  b.tile_y = tile[1];
+  b.tile_z = tile[2];
+  b.tiles_x = (b.nx + tile[0] - 1) / tile[0];
+  b.tiles_y = (b.ny + tile[1] - 1) / tile[1];
+  b.tiles_z = (b.nz + tile[2] - 1) / tile[2];
+  b.frame_tiles = (F + shp.frame_tile - 1) / shp.frame_tile;
+  (void)V;
+  if (b.frame_tiles > 65535) return MACH_ERR_UNSUPPORTED;   // grid y limit
+  if (static_cast<int64_t>(b.tiles_x) * b.tiles_y * b.tiles_z > INT32_MAX) return MACH_ERR_UNSUPPORTED;
+  return MACH_OK;
+}
+
 mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) {
   if (!out) return MACH_ERR_INVALID_ARG;
   *out = nullptr;
@@ -174,16 +237,32 @@ mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) 
   const bool list = d->vox_pos != nullptr;
   const int64_t V = list ? d->n_vox
                          : static_cast<int64_t>(d->grid_dims[0]) * d->grid_dims[1] * d->grid_dims[2];
-  const Variant var = pick_variant(d->iq_dtype, F);
-  const VariantShape& shp = variant_shape(var);
-  const int frame_tiles = (F + shp.frame_tile - 1) / shp.frame_tile;
-  const int per_cta = shp.voxels_per_warp * shp.warps;
-  if (frame_tiles > 65535) return MACH_ERR_UNSUPPORTED;   // grid y limit
+  if (list && V > INT32_MAX) return MACH_ERR_UNSUPPORTED;
+  Variant var = pick_variant(d->iq_dtype, F);
+  const bool forced = g_force_variant >= 0;
+  if (forced) {
+    if (g_force_variant >= V_COUNT || !variant_accepts(static_cast<Variant>(g_force_variant), d->iq_dtype, F))
+      return MACH_ERR_UNSUPPORTED;
+    var = static_cast<Variant>(g_force_variant);
+  }
+
+  DasParams b{};
+  if (list) {
+    b.nx = static_cast<int>(V);
+    b.ny = b.nz = 1;
+  } else {
+    b.nx = d->grid_dims[0];
+    b.ny = d->grid_dims[1];
+    b.nz = d->grid_dims[2];
+  }
+  if ((st = configure_tiles(b, var, list, V, F)) != MACH_OK) return st;
+  const int64_t tiles0 = static_cast<int64_t>(b.tiles_x) * b.tiles_y * b.tiles_z;
 
   // host-side size check before touching the device
   const size_t need = static_cast<size_t>(V) * (sizeof(float4) + sizeof(float) * T) + sizeof(float4) * C +
-                      (frame_tiles > 1 ? sizeof(float) * V * frame_tiles : 0) +
-                      (list ? sizeof(float) * 3 * V : 0) + sizeof(double) * 3 * T;
+                      (b.frame_tiles > 1 ? sizeof(float) * V * b.frame_tiles : 0) +
+                      (list ? sizeof(float) * 3 * V : 0) + sizeof(double) * 3 * T +
+                      (variant_shape(var).staged ? static_cast<size_t>(tiles0) * (2 * sizeof(float4) + T * sizeof(float2)) : 0);
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
     cudaGetLastError();
@@ -222,24 +301,28 @@ mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) 
 
   float* d_raw = nullptr;
   double* d_u = nullptr;
+  int* d_stats = nullptr;
   int64_t scratch_bytes = 0;
   auto fail = [&](mach_status e) {
     cudaFree(d_raw);
     cudaFree(d_u);
+    cudaFree(d_stats);
     release(p);
     return e;
   };
   if ((st = dev_alloc(reinterpret_cast<void**>(&p->d_vox), sizeof(float4) * V, &p->device_bytes)) != MACH_OK) return fail(st);
   if ((st = dev_alloc(reinterpret_cast<void**>(&p->d_elem), sizeof(float4) * C, &p->device_bytes)) != MACH_OK) return fail(st);
   if ((st = dev_alloc(reinterpret_cast<void**>(&p->d_tx), sizeof(float) * T * V, &p->device_bytes)) != MACH_OK) return fail(st);
-  if (frame_tiles > 1 &&
-      (st = dev_alloc(reinterpret_cast<void**>(&p->d_pd_part), sizeof(float) * frame_tiles * V, &p->device_bytes)) != MACH_OK)
+  if ((st = dev_alloc(reinterpret_cast<void**>(&p->d_err), sizeof(int), &p->device_bytes)) != MACH_OK) return fail(st);
+  if (b.frame_tiles > 1 &&
+      (st = dev_alloc(reinterpret_cast<void**>(&p->d_pd_part), sizeof(float) * b.frame_tiles * V, &p->device_bytes)) != MACH_OK)
     return fail(st);
   if (list && (st = dev_alloc(reinterpret_cast<void**>(&d_raw), sizeof(float) * 3 * V, &scratch_bytes)) != MACH_OK)
     return fail(st);
   if (!u.empty() && (st = dev_alloc(reinterpret_cast<void**>(&d_u), sizeof(double) * u.size(), &scratch_bytes)) != MACH_OK)
     return fail(st);
 
+  if (cudaMemsetAsync(p->d_err, 0, sizeof(int), s) != cudaSuccess) return fail(MACH_ERR_CUDA);
   if (cudaMemcpyAsync(p->d_elem, elem.data(), sizeof(float4) * C, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return fail(MACH_ERR_CUDA);
   if (list && cudaMemcpyAsync(d_raw, d->vox_pos, sizeof(float) * 3 * V, cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -266,13 +349,7 @@ mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) 
   tp.vox_out = p->d_vox;
   tp.tx_out = p->d_tx;
   if (launch_tables(tp, s) != cudaSuccess) return fail(MACH_ERR_CUDA);
-  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(MACH_ERR_CUDA);
-  cudaFree(d_raw);
-  cudaFree(d_u);
-  d_raw = nullptr;
-  d_u = nullptr;
 
-  DasParams& b = p->base;
   b.vox = p->d_vox;
   b.elem = p->d_elem;
   b.tx = p->d_tx;
@@ -282,24 +359,6 @@ mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) 
   b.T = T;
   b.S = S;
   b.F = F;
-  if (list) {
-    b.nx = static_cast<int>(std::min<int64_t>(V, INT32_MAX));
-    b.ny = b.nz = 1;
-  } else {
-    b.nx = d->grid_dims[0];
-    b.ny = d->grid_dims[1];
-    b.nz = d->grid_dims[2];
-  }
-  if (list && V > INT32_MAX) return fail(MACH_ERR_UNSUPPORTED);
-  int tile[3];
-  pick_tile(per_cta, b.nx, b.ny, b.nz, list, tile);
-  b.tile_x = tile[0];
-  b.tile_y = tile[1];
-  b.tile_z = tile[2];
-  b.tiles_x = (b.nx + tile[0] - 1) / tile[0];
-  b.tiles_y = (b.ny + tile[1] - 1) / tile[1];
-  b.tiles_z = (b.nz + tile[2] - 1) / tile[2];
-  if (static_cast<int64_t>(b.tiles_x) * b.tiles_y * b.tiles_z > INT32_MAX) return fail(MACH_ERR_UNSUPPORTED);
   b.apod = d->apod;
   b.two_f = static_cast<float>(2.0 * d->f_number);
   b.f_num = static_cast<float>(d->f_number);
@@ -307,7 +366,51 @@ mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) 
   b.r_f = static_cast<float>(d->fc / d->fs);
   b.phase_R = fixed_cycles(d->fc / d->fs);
   b.phase_Phi = fixed_cycles(d->fc * d->t0);
-  b.frame_tiles = frame_tiles;
+  b.err = p->d_err;
+  b.wait_limit = g_wait_limit ? g_wait_limit : kDefaultWaitLimit;
+  b.debug_stall = g_stall;
+
+  if (variant_shape(var).staged) {
+    // per-tile bounds, ring size, and the number of windows one run copies
+    if ((st = dev_alloc(reinterpret_cast<void**>(&p->d_tbox), sizeof(float4) * 2 * tiles0, &p->device_bytes)) != MACH_OK)
+      return fail(st);
+    if ((st = dev_alloc(reinterpret_cast<void**>(&p->d_txr), sizeof(float2) * T * tiles0, &p->device_bytes)) != MACH_OK)
+      return fail(st);
+    if ((st = dev_alloc(reinterpret_cast<void**>(&d_stats), 2 * sizeof(int), &scratch_bytes)) != MACH_OK) return fail(st);
+    if (launch_tile_bounds(b, p->d_tbox, p->d_txr, d_stats, s) != cudaSuccess) return fail(MACH_ERR_CUDA);
+    int stats[2] = {0, 0};
+    if (cudaMemcpyAsync(stats, d_stats, sizeof(stats), cudaMemcpyDeviceToHost, s) != cudaSuccess) return fail(MACH_ERR_CUDA);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(MACH_ERR_CUDA);
+    p->rows_cap = std::max(2, stats[0]);
+    p->copy_pairs = stats[1];
+    b.tbox = p->d_tbox;
+    b.txr = p->d_txr;
+    b.rows_cap = p->rows_cap;
+    if (staged_smem_bytes(var, p->rows_cap, F) > kStagedSmemCap) {
+      if (forced) return fail(MACH_ERR_UNSUPPORTED);
+      // the tiles' windows are too long for the ring: use the L1-cached variant
+      cudaFree(p->d_tbox);
+      cudaFree(p->d_txr);
+      p->d_tbox = nullptr;
+      p->d_txr = nullptr;
+      b.tbox = nullptr;
+      b.txr = nullptr;
+      p->device_bytes -= static_cast<int64_t>(sizeof(float4) * 2 * tiles0 + sizeof(float2) * T * tiles0);
+      var = unstaged(var);
+      p->variant = var;
+      p->rows_cap = 0;
+      p->copy_pairs = 0;
+      if ((st = configure_tiles(b, var, list, V, F)) != MACH_OK) return fail(st);
+    }
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(MACH_ERR_CUDA);
+  cudaFree(d_raw);
+  cudaFree(d_u);
+  cudaFree(d_stats);
+  d_raw = nullptr;
+  d_u = nullptr;
+  d_stats = nullptr;
+  p->base = b;
   *out = p;
   return MACH_OK;
 }
@@ -320,6 +423,10 @@ mach_status mach_plan_destroy(mach_plan p) {
 
 static mach_status run(mach_plan p, const void* iq, float* pd, void* y, void* stream) {
   if (!p || !iq || (!pd && !y)) return MACH_ERR_INVALID_ARG;
+  // vector loads and bulk copies need 16-byte aligned IQ; outputs are float2 / float4
+  if ((reinterpret_cast<uintptr_t>(iq) & 15u) || (reinterpret_cast<uintptr_t>(y) & 15u) ||
+      (reinterpret_cast<uintptr_t>(pd) & 3u))
+    return MACH_ERR_INVALID_ARG;
   DasParams q = p->base;
   q.iq = iq;
   q.y = static_cast<float2*>(y);
@@ -355,8 +462,44 @@ mach_status mach_plan_get_info(mach_plan p, mach_plan_info* info) {
   info->ctas = static_cast<int64_t>(p->base.tiles_x) * p->base.tiles_y * p->base.tiles_z * p->base.frame_tiles;
   info->smem_bytes = static_cast<int64_t>(das_smem_bytes(p->variant));
   info->device_bytes = p->device_bytes;
+  info->ring_rows = p->rows_cap;
+  info->ring_slots = variant_shape(p->variant).ring_slots;
+  info->copy_pairs = p->copy_pairs;
+  if (variant_shape(p->variant).staged) {
+    info->smem_bytes = static_cast<int64_t>(staged_smem_bytes(p->variant, p->rows_cap, p->base.F));
+    info->threads_per_cta = (s.warps + 1) * 32;
+  }
   return MACH_OK;
 }
+
+mach_status mach_plan_device_status(mach_plan p, void* stream) {
+  if (!p) return MACH_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int err = 0;
+  if (cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MACH_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MACH_ERR_CUDA;
+  if (err == 0) return MACH_OK;
+  if (cudaMemsetAsync(p->d_err, 0, sizeof(int), s) != cudaSuccess) return MACH_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MACH_ERR_CUDA;
+  return MACH_ERR_TIMEOUT;
+}
+
+mach_status mach_debug_force_variant(const char* name) {
+  if (!name || !*name) {
+    g_force_variant = -1;
+    return MACH_OK;
+  }
+  for (int v = 0; v < V_COUNT; ++v)
+    if (std::strcmp(variant_shape(static_cast<Variant>(v)).name, name) == 0) {
+      g_force_variant = v;
+      return MACH_OK;
+    }
+  return MACH_ERR_INVALID_ARG;
+}
+
+void mach_debug_set_wait_limit(uint32_t polls) { g_wait_limit = polls; }
+
+void mach_debug_stall_producer(int32_t on) { g_stall = on ? 1 : 0; }
 
 mach_status mach_plan_tx_table(mach_plan p, float* out_dev, void* stream) {
   if (!p || !out_dev) return MACH_ERR_INVALID_ARG;

@@ -154,7 +154,7 @@ def test_doppler2d_full_all_voxels():
     """The benchmark workload, in the launch configuration the benchmark times."""
     acq, iq = synth.make("doppler2d", "full", device="cuda")
     with plan_for(acq) as p:
-        assert p.info()["variant"] == "frames_c64_ft32"
+        assert p.info()["variant"] in ("staged_c64_ft32", "frames_c64_ft32")
         pd, y = p.power_doppler(iq, want_y=True)
     print(compare(acq, iq.cpu(), y, pd))
 
@@ -333,3 +333,96 @@ def test_oversize_plan_is_refused_before_allocating():
     with pytest.raises(m.MachError) as e:
         plan_for(acq.replace(tx_angles=np.zeros((512, 2))))
     assert e.value.status == m.MACH_ERR_OOM
+
+
+# ------------------------------------------------------ kernel variants ----
+
+def forced(acq, name):
+    m.mach_debug_force_variant(name)
+    try:
+        return plan_for(acq)
+    finally:
+        m.mach_debug_force_variant(None)
+
+
+STAGED_CASES = [
+    ("staged_c64_ft32", "frames_c64_ft32", "doppler2d", "c64"),
+    ("staged_c64_ft32_v4", "frames_c64_ft32", "doppler2d", "c64"),
+    ("staged_c64_ft64", "frames_c64_ft64", "volume3d", "c64"),
+    ("staged_f16_ft32", "frames_f16_ft32", "doppler2d", "f16x2"),
+    ("staged_f16_ft64", "frames_f16_ft64", "volume3d", "f16x2"),
+]
+
+
+@pytest.mark.parametrize("staged,l1,name,dt", STAGED_CASES)
+def test_staged_matches_oracle_and_l1_kernel_bitwise(staged, l1, name, dt):
+    """The staged kernel reads the same taps from shared memory that the L1 kernel reads
+    from global memory and accumulates the terms in the same order: identical bits."""
+    acq, iq = synth.make(name, "small", device="cuda", iq_dtype=dt)
+    diq = dev_iq(acq, iq)
+    with forced(acq, staged) as ps, forced(acq, l1) as pl:
+        assert ps.info()["variant"] == staged and pl.info()["variant"] == l1
+        info = ps.info()
+        assert info["ring_rows"] >= 2 and info["copy_pairs"] > 0
+        pd_s, y_s = ps.power_doppler(diq, want_y=True)
+        pd_l, y_l = pl.power_doppler(diq, want_y=True)
+        torch.cuda.synchronize()
+        assert ps.device_status() == m.MACH_OK
+    assert torch.equal(y_s, y_l) and torch.equal(pd_s, pd_l)
+    ref_iq = synth.iqmod.from_f16x2(diq.cpu()) if dt == "f16x2" else iq.cpu()
+    print(staged, info["ring_rows"], info["copy_pairs"], compare(acq, ref_iq, y_s, pd_s))
+
+
+@pytest.mark.parametrize("F", [18, 20, 30, 32, 34, 48, 62, 64])
+def test_staged_partial_frame_tiles(F):
+    acq = small_random(F, C=17, T=3)
+    iq = synth.random_iq(acq, F, device="cuda")
+    with plan_for(acq) as p:
+        assert p.info()["variant"].startswith("staged")
+        pd, y = p.power_doppler(iq, want_y=True)
+    compare(acq, iq.cpu(), y, pd)
+
+
+def test_staged_full_doppler_bitwise_equal_to_l1():
+    acq, iq = synth.make("doppler2d", "full", device="cuda")
+    with forced(acq, "staged_c64_ft32") as ps, forced(acq, "frames_c64_ft32") as pl:
+        pd_s, y_s = ps.power_doppler(iq, want_y=True)
+        pd_l, y_l = pl.power_doppler(iq, want_y=True)
+        torch.cuda.synchronize()
+        print(ps.info())
+    assert torch.equal(y_s, y_l) and torch.equal(pd_s, pd_l)
+
+
+def test_forced_variant_rejections():
+    acq = synth.make_acquisition("doppler2d", "small")
+    with pytest.raises(m.MachError):
+        m.mach_debug_force_variant("no_such_variant")
+    m.mach_debug_force_variant("staged_f16_ft32")    # wrong storage type for this plan
+    try:
+        with pytest.raises(m.MachError) as e:
+            plan_for(acq)
+        assert e.value.status == m.MACH_ERR_UNSUPPORTED
+    finally:
+        m.mach_debug_force_variant(None)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """The producer announces its copies but never issues them: every consumer wait runs
+    out (bounded), the kernel sets the error word and returns; the host reads
+    MACH_ERR_TIMEOUT, and the same context then beamforms correctly."""
+    acq, iq = synth.make("doppler2d", "small", device="cuda")
+    m.mach_debug_set_wait_limit(2000)
+    m.mach_debug_stall_producer(True)
+    try:
+        with plan_for(acq) as p:
+            assert p.info()["variant"].startswith("staged")
+            pd, y = p.power_doppler(iq, want_y=True)
+            assert p.device_status() == m.MACH_ERR_TIMEOUT
+            assert p.device_status() == m.MACH_OK          # cleared
+    finally:
+        m.mach_debug_stall_producer(False)
+        m.mach_debug_set_wait_limit(0)
+    with plan_for(acq) as p:
+        pd, y = p.power_doppler(iq, want_y=True)
+        assert p.device_status() == m.MACH_OK
+    compare(acq, iq.cpu(), y, pd)
