@@ -196,6 +196,22 @@ def oracle_sample(acq, iq_host, seconds, min_vox=64):
                       f"and frames; one pass, {dt:.2f} s, FP64"}
 
 
+def count_active_terms(plan, V, C, T, chunk_terms=1 << 26):
+    """Terms (voxel, element, transmit) inside the aperture and the sample range, as the
+    kernels evaluate them (mach_das_terms, indices only, in voxel chunks)."""
+    import torch
+    import paper_2604_06257_gb300 as m
+    per = max(1, chunk_terms // (C * T))
+    i0 = torch.empty(min(per, V) * C * T, dtype=torch.int32, device="cuda")
+    total = 0
+    for a in range(0, V, per):
+        n = min(per, V - a)
+        idx = torch.arange(a, a + n, dtype=torch.int64, device="cuda")
+        m.mach_das_terms(plan.handle, idx, i0=i0[: n * C * T])
+        total += int((i0[: n * C * T] >= 0).sum().item())
+    return total
+
+
 # ---------------------------------------------------------------- our arm ----
 
 def run_ours(args):
@@ -226,8 +242,7 @@ def run_ours(args):
     pd = torch.empty(V, dtype=torch.float32, device=dev)
     y = torch.empty((V, F), dtype=torch.complex64, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    i0, _, _ = plan.terms(np.arange(V))
-    active_terms = int((i0 >= 0).sum().item())
+    active_terms = count_active_terms(plan, V, acq.n_elem, acq.n_tx)
     active_points = active_terms * F
     launches_per_step = 1 + (1 if info["frame_tiles"] > 1 else 0)
     stream = torch.cuda.current_stream()

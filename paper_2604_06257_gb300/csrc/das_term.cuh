@@ -89,6 +89,19 @@ __device__ __forceinline__ int64_t tile_voxel(const DasParams& p, int64_t tile, 
   return gx + static_cast<int64_t>(p.nx) * (gy + static_cast<int64_t>(p.ny) * gz);
 }
 
+// Voxel of slot q when each warp owns a compact wb_x x wb_y x wb_z block of the tile
+// (the tile is a whole number of such blocks); -1 past the grid edge.
+__device__ __forceinline__ int64_t tile_voxel_blocked(const DasParams& p, int64_t tile, int q) {
+  if (p.wb_x == 0) return tile_voxel(p, tile, q);
+  const int wbv = p.wb_x * p.wb_y * p.wb_z;
+  const int b = q / wbv, r = q % wbv;
+  const int nbx = p.tile_x / p.wb_x, nby = p.tile_y / p.wb_y;
+  const int lx = (b % nbx) * p.wb_x + r % p.wb_x;
+  const int ly = ((b / nbx) % nby) * p.wb_y + (r / p.wb_x) % p.wb_y;
+  const int lz = (b / (nbx * nby)) * p.wb_z + r / (p.wb_x * p.wb_y);
+  return tile_voxel(p, tile, lx + p.tile_x * (ly + p.tile_y * lz));
+}
+
 // Sample rows [lo, lo + rows) of element e that the voxels of a tile can touch for one
 // transmit, from the tile's bounding box (sample units) and its transmit-delay range:
 // the receive delay over the box lies between the distances from e to the nearest and

@@ -169,32 +169,66 @@ __device__ __forceinline__ void mac_st(float2& acc, float c0r, float c0i, float 
 }
 
 // ---- the staged kernel --------------------------------------------------------------------
+constexpr int kTxCache = 16;   // transmits whose delays are cached in shared memory per warp
+
+// Shared memory: [ring slots][term tables][transmit-delay cache][slot metadata][barriers]
 template <int NBUF>
 struct RingLayout {
-  size_t slot_bytes;
-  __host__ __device__ RingLayout(int rows_cap, int F, int iq_bytes)
-      : slot_bytes(((static_cast<size_t>(rows_cap) * F * iq_bytes) + 127) / 128 * 128) {}
+  size_t slot_bytes, tx_bytes;
+  __host__ __device__ RingLayout(int rows_cap, int F, int iq_bytes, int T, int nwc)
+      : slot_bytes(((static_cast<size_t>(rows_cap) * F * iq_bytes) + 127) / 128 * 128),
+        tx_bytes(T <= kTxCache ? static_cast<size_t>(nwc) * T * 32 * 4 : 0) {}
   __host__ __device__ size_t terms_off() const { return NBUF * slot_bytes; }
-  __host__ __device__ size_t meta_off(int nwc) const { return terms_off() + static_cast<size_t>(nwc) * 32 * 16; }
-  __host__ __device__ size_t bar_off(int nwc) const { return meta_off(nwc) + NBUF * 16; }
+  __host__ __device__ size_t tx_off(int nwc) const { return terms_off() + static_cast<size_t>(nwc) * 32 * 16; }
+  __host__ __device__ size_t meta_off(int nwc) const { return tx_off(nwc) + (tx_bytes + 15) / 16 * 16; }
+  __host__ __device__ size_t bar_off(int nwc) const { return meta_off(nwc) + NBUF * 32; }
   __host__ __device__ size_t total(int nwc) const { return bar_off(nwc) + 2 * NBUF * 8; }
 };
 
+// Slot metadata published by the producer with each window.
+struct SlotMeta {
+  int t, c, lo, rows;   // c < 0: end of sequence
+  float4 e;             // element position (sample units)
+};
+
+template <class IQ, int VEC, int NV, int FL>
+__device__ __forceinline__ void gather_mac(float2 (&acc)[VEC * NV], const IQ* r0, int F, int f_base, int jl,
+                                           float c0r, float c0i, float c1r, float c1i, bool smem) {
+#pragma unroll
+  for (int mm = 0; mm < NV; ++mm) {
+    const int f = f_base + (jl + FL * mm) * VEC;
+    if (f < F) {
+      float2 x0[VEC], x1[VEC];
+      if (smem) {
+        SmemVec<IQ, VEC>::load(r0 + f, x0);
+        SmemVec<IQ, VEC>::load(r0 + F + f, x1);
+      } else {
+        GlobVec<IQ, VEC>::load(r0 + f, x0);
+        GlobVec<IQ, VEC>::load(r0 + F + f, x1);
+      }
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) mac_st(acc[mm * VEC + e], c0r, c0i, c1r, c1i, x0[e], x1[e]);
+    }
+  }
+}
+
 template <class IQ, int VEC, int NV, int FL, int VPG, int NWC, int NBUF, int MINB>
-__global__ void __launch_bounds__((NWC + 1) * 32, MINB) k_das_staged(const DasParams p) {
+__global__ void __launch_bounds__((NWC + 1) * 32) __maxnreg__(MINB == 2 ? 112 : (MINB == 3 ? 72 : 168)) k_das_staged(const DasParams p) {
   constexpr int G = 32 / FL;
   constexpr int WV = G * VPG;
   constexpr int FPL = VEC * NV;
   constexpr int FT = FL * FPL;
   static_assert(WV <= 32, "one term per lane and pair");
   extern __shared__ __align__(128) unsigned char smem[];
-  const RingLayout<NBUF> L(p.rows_cap, p.F, static_cast<int>(sizeof(IQ)));
+  const RingLayout<NBUF> L(p.rows_cap, p.F, static_cast<int>(sizeof(IQ)), p.T, NWC);
   IQ* ring = reinterpret_cast<IQ*>(smem);
   float4* terms_all = reinterpret_cast<float4*>(smem + L.terms_off());
-  int4* meta = reinterpret_cast<int4*>(smem + L.meta_off(NWC));
+  float* txc_all = reinterpret_cast<float*>(smem + L.tx_off(NWC));
+  SlotMeta* meta = reinterpret_cast<SlotMeta*>(smem + L.meta_off(NWC));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bar_off(NWC));
   uint64_t* empty = full + NBUF;
   const size_t slot_elems = L.slot_bytes / sizeof(IQ);
+  const bool tx_cached = p.T <= kTxCache;
 
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -229,7 +263,11 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB) k_das_staged(const DasPa
           ok = false;
           break;
         }
-        meta[slot] = make_int4(t, c, lo, rows);
+        meta[slot].t = t;
+        meta[slot].c = c;
+        meta[slot].lo = lo;
+        meta[slot].rows = rows;
+        meta[slot].e = e;
         const uint32_t bytes = static_cast<uint32_t>(rows) * p.F * sizeof(IQ);
         mbar_arrive_expect_tx(&full[slot], bytes);
         if (!p.debug_stall)
@@ -243,7 +281,7 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB) k_das_staged(const DasPa
       if (r >= NBUF && !mbar_wait_bounded(&empty[slot], ((r / NBUF) - 1) & 1, p.wait_limit)) {
         atomicOr(p.err, 1);
       } else {
-        meta[slot] = make_int4(-1, -1, 0, 0);
+        meta[slot].c = -1;
         mbar_arrive(&full[slot]);
       }
     } else {    // abandoning: let the copies already issued land before the block can exit
@@ -257,12 +295,15 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB) k_das_staged(const DasPa
   const int jl = lane % FL;
   const int f_base = blockIdx.y * FT;
   float4* terms = terms_all + warp * 32;
-  // term slot of this lane: voxel lane (if lane < WV); stored at k*G + g so that the G
-  // groups of a warp read G consecutive entries (no bank conflict)
-  const int q_lane = lane;
-  const int64_t v_term = lane < WV ? tile_voxel(p, tile, warp * WV + q_lane) : -1;
+  float* txc = txc_all + warp * (p.T * 32);
+  // lane < WV evaluates the terms of voxel slot `lane`; they are stored at k*G + g so
+  // that the G groups of the warp read G consecutive entries (no bank conflict)
+  const int64_t v_term = lane < WV ? tile_voxel_blocked(p, tile, warp * WV + lane) : -1;
   const float4 vpos = v_term >= 0 ? p.vox[v_term] : make_float4(0.f, 0.f, 0.f, 0.f);
-  const int store_at = (q_lane % VPG) * G + (q_lane / VPG);
+  const int store_at = (lane % VPG) * G + (lane / VPG);
+  if (tx_cached) {
+    for (int t = 0; t < p.T; ++t) txc[t * 32 + lane] = v_term >= 0 ? p.tx[static_cast<size_t>(t) * p.V + v_term] : 0.f;
+  }
 
   float2 acc[VPG][FPL];
 #pragma unroll
@@ -282,54 +323,55 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB) k_das_staged(const DasPa
       ok = false;
       break;
     }
-    const int4 m = meta[slot];
-    if (m.y < 0) break;
-    const int t = m.x, c = m.y, lo = m.z, rows = m.w;
-    if (c != cur_c) {
-      cur_c = c;
+    const SlotMeta m = meta[slot];
+    if (m.c < 0) break;
+    if (m.c != cur_c) {
+      cur_c = m.c;
       geo.a = -1.f;
-      if (v_term >= 0) geo = term_geometry(vpos, __ldg(&p.elem[c]), p);
+      if (v_term >= 0) geo = term_geometry(vpos, m.e, p);
     }
     float4 rec = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
-    if (geo.a >= 0.f) rec = term_record(__ldg(&p.tx[static_cast<size_t>(t) * p.V + v_term]), geo, p);
-    __syncwarp();
-    if (lane < WV) terms[store_at] = rec;
-    __syncwarp();
-    const IQ* win = ring + slot * slot_elems;
-    const IQ* gsrc = iq + (static_cast<size_t>(t) * p.C + c) * slab;
+    if (geo.a >= 0.f) {
+      const float stx = tx_cached ? txc[m.t * 32 + lane] : __ldg(&p.tx[static_cast<size_t>(m.t) * p.V + v_term]);
+      rec = term_record(stx, geo, p);
+    }
+    const int my_i0 = __float_as_int(rec.w);
+    const bool active = my_i0 >= 0;
+    const bool outside = active && (my_i0 - m.lo < 0 || my_i0 - m.lo + 1 >= m.rows);
+    const unsigned any_active = __ballot_sync(0xffffffffu, active);
+    const unsigned any_outside = __ballot_sync(0xffffffffu, outside);
+    if (any_active) {
+      if (lane < WV) terms[store_at] = rec;
+      __syncwarp();
+      const IQ* win = ring + slot * slot_elems;
+      if (!any_outside) {
+        // every kept term lies in the staged window: branch-free over the voxels
+        // (dropped terms carry zero weights and read row 0)
 #pragma unroll
-    for (int k = 0; k < VPG; ++k) {
-      const float4 tr = terms[k * G + g];
-      const int i0 = __float_as_int(tr.w);
-      if (i0 >= 0) {
-        const float c1r = tr.x * tr.z, c1i = tr.y * tr.z;
-        const float c0r = tr.x - c1r, c0i = tr.y - c1i;
-        const int row = i0 - lo;
-        if (row >= 0 && row + 1 < rows) {
-          const IQ* r0 = win + row * p.F;
+        for (int k = 0; k < VPG; ++k) {
+          const float4 tr = terms[k * G + g];
+          const int row = max(__float_as_int(tr.w) - m.lo, 0);
+          const float c1r = tr.x * tr.z, c1i = tr.y * tr.z;
+          const float c0r = tr.x - c1r, c0i = tr.y - c1i;
+          gather_mac<IQ, VEC, NV, FL>(acc[k], win + row * p.F, p.F, f_base, jl, c0r, c0i, c1r, c1i, true);
+        }
+      } else {
+        // some kept term falls outside the staged window (not expected): per-term
+        // choice between the window and global memory
+        const IQ* gsrc = iq + (static_cast<size_t>(m.t) * p.C + m.c) * slab;
 #pragma unroll
-          for (int mm = 0; mm < NV; ++mm) {
-            const int f = f_base + (jl + FL * mm) * VEC;
-            if (f < p.F) {
-              float2 x0[VEC], x1[VEC];
-              SmemVec<IQ, VEC>::load(r0 + f, x0);
-              SmemVec<IQ, VEC>::load(r0 + p.F + f, x1);
-#pragma unroll
-              for (int e = 0; e < VEC; ++e) mac_st(acc[k][mm * VEC + e], c0r, c0i, c1r, c1i, x0[e], x1[e]);
-            }
-          }
-        } else {   // outside the staged window (not expected): read the taps from global memory
-          const IQ* r0 = gsrc + static_cast<size_t>(i0) * p.F;
-#pragma unroll
-          for (int mm = 0; mm < NV; ++mm) {
-            const int f = f_base + (jl + FL * mm) * VEC;
-            if (f < p.F) {
-              float2 x0[VEC], x1[VEC];
-              GlobVec<IQ, VEC>::load(r0 + f, x0);
-              GlobVec<IQ, VEC>::load(r0 + p.F + f, x1);
-#pragma unroll
-              for (int e = 0; e < VEC; ++e) mac_st(acc[k][mm * VEC + e], c0r, c0i, c1r, c1i, x0[e], x1[e]);
-            }
+        for (int k = 0; k < VPG; ++k) {
+          const float4 tr = terms[k * G + g];
+          const int i0 = __float_as_int(tr.w);
+          if (i0 >= 0) {
+            const float c1r = tr.x * tr.z, c1i = tr.y * tr.z;
+            const float c0r = tr.x - c1r, c0i = tr.y - c1i;
+            const int row = i0 - m.lo;
+            if (row >= 0 && row + 1 < m.rows)
+              gather_mac<IQ, VEC, NV, FL>(acc[k], win + row * p.F, p.F, f_base, jl, c0r, c0i, c1r, c1i, true);
+            else
+              gather_mac<IQ, VEC, NV, FL>(acc[k], gsrc + static_cast<size_t>(i0) * p.F, p.F, f_base, jl, c0r, c0i,
+                                          c1r, c1i, false);
           }
         }
       }
@@ -341,7 +383,7 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB) k_das_staged(const DasPa
 
 #pragma unroll
   for (int k = 0; k < VPG; ++k) {
-    const int64_t v = tile_voxel(p, tile, warp * WV + g * VPG + k);
+    const int64_t v = tile_voxel_blocked(p, tile, warp * WV + g * VPG + k);
     float pw = 0.f;
 #pragma unroll
     for (int mm = 0; mm < NV; ++mm) {
@@ -383,13 +425,13 @@ cudaError_t go_staged(K kernel, const DasParams& p, size_t smem, cudaStream_t s)
 }
 }  // namespace
 
-size_t staged_smem_bytes(Variant v, int rows_cap, int F) {
+size_t staged_smem_bytes(Variant v, int rows_cap, int F, int T) {
   const int b = (v == V_ST32_H16 || v == V_ST64_H16) ? 4 : 8;
-  return RingLayout<kRing>(rows_cap, F, b).total(kNWC);
+  return RingLayout<kRing>(rows_cap, F, b, T, kNWC).total(kNWC);
 }
 
 cudaError_t launch_das_staged(const DasParams& p, Variant v, cudaStream_t s) {
-  const size_t sm = staged_smem_bytes(v, p.rows_cap, p.F);
+  const size_t sm = staged_smem_bytes(v, p.rows_cap, p.F, p.T);
   switch (v) {
     case V_ST32_C64: return go_staged(k_das_staged<float2, 2, 2, 8, 8, kNWC, kRing, 2>, p, sm, s);
     case V_ST64_C64: return go_staged(k_das_staged<float2, 2, 2, 16, 8, kNWC, kRing, 2>, p, sm, s);

@@ -75,6 +75,7 @@ struct DasParams {
   uint32_t wait_limit;  // polls before a wait gives up
   int* err;             // device error word (bit 0: a wait timed out)
   int debug_stall;      // test hook: the producer announces copies but never issues them
+  int wb_x, wb_y, wb_z; // staged variants: voxel block of one warp inside the tile (0: row-major)
 };
 
 // Tables built once per plan (kernel K1).
@@ -99,7 +100,7 @@ cudaError_t launch_das(const DasParams& p, Variant v, cudaStream_t s);
 // number of (tile, transmit, element) triples that need a copy.
 cudaError_t launch_tile_bounds(const DasParams& p, float4* tbox, float2* txr, int* d_rows_pairs,
                                cudaStream_t s);
-size_t staged_smem_bytes(Variant v, int rows_cap, int F);
+size_t staged_smem_bytes(Variant v, int rows_cap, int F, int T);
 cudaError_t launch_das_staged(const DasParams& p, Variant v, cudaStream_t s);
 cudaError_t launch_terms(const DasParams& p, const int64_t* vox_idx, int64_t n, int32_t* i0,
                          float* w, float* cw, cudaStream_t s);

@@ -221,6 +221,25 @@ static mach_status configure_tiles(DasParams& b, Variant var, bool list, int64_t
   b.tiles_z = (b.nz + tile[2] - 1) / tile[2];
   b.frame_tiles = (F + shp.frame_tile - 1) / shp.frame_tile;
   (void)V;
+  // staged kernels: each warp owns a compact block of the tile, so that its voxels tend to
+  // agree on which (element, transmit) pairs they use (the warp skips pairs none of them use)
+  b.wb_x = b.wb_y = b.wb_z = 0;
+  if (shp.staged && !list && !(b.ny == 1 && b.nz == 1)) {
+    int wb[3] = {0, 0, 0};
+    const int wv = shp.voxels_per_warp;
+    if (b.ny == 1) {
+      if (wv == 32) { wb[0] = 8; wb[1] = 1; wb[2] = 4; }
+      else if (wv == 16) { wb[0] = 4; wb[1] = 1; wb[2] = 4; }
+    } else {
+      if (wv == 32) { wb[0] = 4; wb[1] = 4; wb[2] = 2; }
+      else if (wv == 16) { wb[0] = 4; wb[1] = 4; wb[2] = 1; }
+    }
+    if (wb[0] && tile[0] % wb[0] == 0 && tile[1] % wb[1] == 0 && tile[2] % wb[2] == 0) {
+      b.wb_x = wb[0];
+      b.wb_y = wb[1];
+      b.wb_z = wb[2];
+    }
+  }
   if (b.frame_tiles > 65535) return MACH_ERR_UNSUPPORTED;   // grid y limit
   if (static_cast<int64_t>(b.tiles_x) * b.tiles_y * b.tiles_z > INT32_MAX) return MACH_ERR_UNSUPPORTED;
   return MACH_OK;
@@ -386,7 +405,7 @@ mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) 
     b.tbox = p->d_tbox;
     b.txr = p->d_txr;
     b.rows_cap = p->rows_cap;
-    if (staged_smem_bytes(var, p->rows_cap, F) > kStagedSmemCap) {
+    if (staged_smem_bytes(var, p->rows_cap, F, T) > kStagedSmemCap) {
       if (forced) return fail(MACH_ERR_UNSUPPORTED);
       // the tiles' windows are too long for the ring: use the L1-cached variant
       cudaFree(p->d_tbox);
@@ -466,7 +485,7 @@ mach_status mach_plan_get_info(mach_plan p, mach_plan_info* info) {
   info->ring_slots = variant_shape(p->variant).ring_slots;
   info->copy_pairs = p->copy_pairs;
   if (variant_shape(p->variant).staged) {
-    info->smem_bytes = static_cast<int64_t>(staged_smem_bytes(p->variant, p->rows_cap, p->base.F));
+    info->smem_bytes = static_cast<int64_t>(staged_smem_bytes(p->variant, p->rows_cap, p->base.F, p->base.T));
     info->threads_per_cta = (s.warps + 1) * 32;
   }
   return MACH_OK;

@@ -363,12 +363,18 @@ def test_staged_matches_oracle_and_l1_kernel_bitwise(staged, l1, name, dt):
     with forced(acq, staged) as ps, forced(acq, l1) as pl:
         assert ps.info()["variant"] == staged and pl.info()["variant"] == l1
         info = ps.info()
+        same_order = pl.info()["voxels_per_cta"] // 8 == 32
         assert info["ring_rows"] >= 2 and info["copy_pairs"] > 0
         pd_s, y_s = ps.power_doppler(diq, want_y=True)
         pd_l, y_l = pl.power_doppler(diq, want_y=True)
         torch.cuda.synchronize()
         assert ps.device_status() == m.MACH_OK
-    assert torch.equal(y_s, y_l) and torch.equal(pd_s, pd_l)
+    if same_order:
+        # one element per round in both kernels: the same FMA sequence per accumulator
+        assert torch.equal(y_s, y_l) and torch.equal(pd_s, pd_l)
+    else:
+        # the L1 kernel takes two elements per round (16 voxels per warp): other order
+        assert nrmse_db(y_s.cpu().numpy(), y_l.cpu().numpy()) < -120
     ref_iq = synth.iqmod.from_f16x2(diq.cpu()) if dt == "f16x2" else iq.cpu()
     print(staged, info["ring_rows"], info["copy_pairs"], compare(acq, ref_iq, y_s, pd_s))
 
