@@ -166,6 +166,27 @@ mach_status mach_das_terms(mach_plan p, const int64_t *vox_idx_dev, int64_t n,
  * times (about a second) and then abandons the block instead of hanging the device. */
 mach_status mach_plan_device_status(mach_plan p, void *stream);
 
+/* Delay-and-sum (and Power Doppler) without allocating device memory.  The paper has
+ * no counterpart: this is for callers that cannot call cudaMalloc -- code running where
+ * the device allocator is off limits (a host callback, a real-time loop that must not
+ * pay an allocation, a host framework that owns all device memory or enforces a memory
+ * budget).  Instead of a plan's tables it uses one fixed device array inside the
+ * library (8 MiB, held on every GPU that loads the library until the process exits).
+ * Same arguments and results as mach_das_plan + mach_das_run / mach_power_doppler on
+ * the non-staged kernels: `d` as for mach_das_plan (host arrays are copied on every
+ * call), iq_dev as for mach_das_run, outputs y_dev_or_null (complex64 [n_vox][n_frames])
+ * and/or pd_dev_or_null (float32 [n_vox]), at least one of them.
+ * Errors: INVALID_ARG as for a plan or a NULL/misaligned buffer; UNSUPPORTED when the
+ * tables (16 B per voxel + 4 B per voxel and transmit + 16 B per element, plus 12 B per
+ * voxel for a voxel list and 4 B per voxel and frame tile for Power Doppler over more
+ * than one frame tile) exceed the 8 MiB array; CUDA.  Nothing is launched on error.
+ * The first call on a device looks up the array's device address (do it before any
+ * stream capture).  Calls share the array, so calls that overlap on the GPU race;
+ * order them on one stream.  Returns after the host arrays are copied; the
+ * beamforming itself is stream-ordered. */
+mach_status mach_das_run_noalloc(const mach_das_desc *d, const void *iq_dev, void *y_dev_or_null,
+                                 float *pd_dev_or_null, void *stream);
+
 /* Library version string, e.g. "mach-gb300 0.1.0 sm_103a". */
 const char *mach_version(void);
 

@@ -29,7 +29,8 @@ IQ_DTYPE = {"c64": 0, "f16x2": 1}
 EXPORTS = ("mach_das_plan", "mach_das_run", "mach_power_doppler", "mach_plan_destroy",
            "mach_status_string", "mach_plan_get_info", "mach_plan_tx_table", "mach_das_terms",
            "mach_version", "mach_debug_fail_alloc_after", "mach_plan_device_status",
-           "mach_debug_force_variant", "mach_debug_set_wait_limit", "mach_debug_stall_producer")
+           "mach_debug_force_variant", "mach_debug_set_wait_limit", "mach_debug_stall_producer",
+           "mach_das_run_noalloc")
 
 
 class MachError(RuntimeError):
@@ -100,6 +101,8 @@ def lib():
         L.mach_debug_set_wait_limit.restype = None
         L.mach_debug_stall_producer.argtypes = [i32]
         L.mach_debug_stall_producer.restype = None
+        L.mach_das_run_noalloc.argtypes = [C.POINTER(mach_das_desc), vp, vp, vp, vp]
+        L.mach_das_run_noalloc.restype = C.c_int
         for f in ("mach_das_plan", "mach_das_run", "mach_power_doppler", "mach_plan_destroy",
                   "mach_plan_get_info", "mach_plan_tx_table", "mach_das_terms"):
             getattr(L, f).restype = C.c_int
@@ -239,6 +242,15 @@ def mach_power_doppler(plan: int, iq, pd, y=None, stream=None) -> None:
                                   _stream_ptr(stream))
     if st != MACH_OK:
         raise MachError(st, "mach_power_doppler")
+
+
+def mach_das_run_noalloc(desc, iq, y=None, pd=None, stream=None) -> None:
+    """Beamform without any device allocation (tables in the library's fixed 8 MiB
+    device array; see include/mach.h)."""
+    st = lib().mach_das_run_noalloc(C.byref(desc), _dev_ptr(iq, "iq"), _dev_ptr(y, "y"),
+                                    _dev_ptr(pd, "pd"), _stream_ptr(stream))
+    if st != MACH_OK:
+        raise MachError(st, "mach_das_run_noalloc")
 
 
 def mach_plan_destroy(plan: int) -> None:

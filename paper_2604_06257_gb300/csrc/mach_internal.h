@@ -106,4 +106,10 @@ cudaError_t launch_terms(const DasParams& p, const int64_t* vox_idx, int64_t n, 
                          float* w, float* cw, cudaStream_t s);
 size_t das_smem_bytes(Variant v);
 
+// Host steps shared by mach_das_plan and the allocation-free entry point.
+mach_status host_validate(const mach_das_desc* d);
+Variant host_unstaged_variant(int iq_dtype, int F);
+mach_status host_configure_tiles(DasParams& b, Variant v, bool list, int64_t V, int F);
+uint32_t host_fixed_cycles(double cycles);
+
 }  // namespace mach

@@ -539,3 +539,15 @@ mach_status mach_das_terms(mach_plan p, const int64_t* vox_idx_dev, int64_t n, i
 }
 
 }  // extern "C"
+
+namespace mach {
+// Host steps shared with the allocation-free entry point (noalloc.cu): the same
+// validation, choice among the non-staged kernels, voxel tiling and phase constants
+// that a plan uses.
+mach_status host_validate(const mach_das_desc* d) { return validate(d); }
+Variant host_unstaged_variant(int iq_dtype, int F) { return unstaged(pick_variant(iq_dtype, F)); }
+mach_status host_configure_tiles(DasParams& b, Variant v, bool list, int64_t V, int F) {
+  return configure_tiles(b, v, list, V, F);
+}
+uint32_t host_fixed_cycles(double cycles) { return fixed_cycles(cycles); }
+}  // namespace mach
