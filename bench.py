@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", default="", help="force a kernel variant (ablations)")
-    ap.add_argument("--iq-dtype", default="c64", choices=["c64", "f16x2"])
+    ap.add_argument("--iq-dtype", default="c64", choices=["c64", "f16x2", "bf16x2", "c64split"])
     return ap.parse_args()
 
 
@@ -231,8 +231,8 @@ def run_ours(args):
 
     acq, iq = synth.make(args.workload, "full", device=dev, seed=synth.SEEDS[args.workload] + rank,
                          iq_dtype=args.iq_dtype)
-    if args.iq_dtype == "f16x2":
-        iq = synth.iqmod.to_f16x2(iq)
+    if args.iq_dtype != "c64":
+        iq = synth.iqmod.to_storage(iq, args.iq_dtype)
     if args.variant:
         m.mach_debug_force_variant(args.variant)
     plan = m.Plan(**m.plan_kwargs(acq))
@@ -289,7 +289,7 @@ def run_ours(args):
     flops = active_points * 16.0                                            # 8 FMA per term-frame
     achieved = flops / t_launch / 1e12
     comp = counts.compulsory_bytes(V, acq.n_elem, acq.n_tx, acq.n_samples, F, write_y=True, write_pd=True,
-                                   iq_bytes=4 if args.iq_dtype == "f16x2" else 8)
+                                   iq_bytes=8 if args.iq_dtype in ("c64", "c64split") else 4)
     traffic = profiled_traffic(info["variant"], acq.name)
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": traffic,
@@ -300,8 +300,35 @@ def run_ours(args):
                            f"and in range: {active_terms} of {V * acq.n_elem * acq.n_tx} terms",
             "hbm": {"compulsory_bytes": comp, "achieved_gbs": comp / t_launch / 1e9,
                     "peak_gbs": hbm_peak, "frac": comp / t_launch / 1e9 / hbm_peak},
-            "sm_load_path": {"bytes_per_term_frame": 16 if args.iq_dtype == "c64" else 8,
-                             "achieved_gbs": active_points * (16 if args.iq_dtype == "c64" else 8) / t_launch / 1e9}}
+            "sm_load_path": {"bytes_per_term_frame": 16 if args.iq_dtype in ("c64", "c64split") else 8,
+                             "achieved_gbs": active_points * (16 if args.iq_dtype in ("c64", "c64split") else 8)
+                             / t_launch / 1e9}}
+
+    # K0 (channel-data preparation): acquisition order -> frame-contiguous layout, per
+    # storage type; HBM-bound, so it is reported against the measured copy bandwidth
+    k0 = {}
+    if args.iq_dtype == "c64":
+        T_, C_, S_, F_ = acq.iq_shape
+        scanner = iq.permute(3, 0, 1, 2).contiguous()
+        n = scanner.numel()
+        for dt, ob in (("c64", 8), ("c64split", 8), ("f16x2", 4), ("bf16x2", 4)):
+            out = m.prepare_iq(scanner, "ftcs", dt)
+            for _ in range(3):
+                m.mach_iq_convert(scanner, "ftcs", out, dt, T_, C_, S_, F_)
+            ts = []
+            for _ in range(20):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                m.mach_iq_convert(scanner, "ftcs", out, dt, T_, C_, S_, F_)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1) / 1e3)
+            t = statistics.median(ts)
+            byts = n * (8 + ob)
+            k0[dt] = {"ms": t * 1e3, "bytes": byts, "achieved_gbs": byts / t / 1e9, "peak_gbs": hbm_peak,
+                      "frac": byts / t / 1e9 / hbm_peak}
+        del scanner, out
 
     # end to end through the public API with host buffers (pinned), copies timed
     e2e = None
@@ -329,11 +356,11 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if args.iq_dtype == "c64" else "f32 (f16 IQ storage)", "data": "synthetic",
+                "dtype": "f32" if args.iq_dtype == "c64" else f"f32 ({args.iq_dtype} IQ storage)", "data": "synthetic",
                 "config": workload_config(acq, {"parallelism": f"replicas{world}",
                                                 "kernel_variant": info["variant"],
                                                 "active_fraction": active_terms / (V * acq.n_elem * acq.n_tx)}),
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "plan": info,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "plan": info, "k0_iq_convert": k0,
                 "gpu_launches": launches_per_step * args.steps,
                 "clocks": clk, "wall_s_timed_region": t_wall,
                 "paper_context": {"points_per_s": PAPER_POINTS_PER_S,

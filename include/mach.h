@@ -15,8 +15,9 @@
  *  - IQ layout in device memory: [n_tx][n_elem][n_samples][n_frames], frames contiguous
  *    (Sec. 4.4 stores [elements, samples, frames]; this ABI adds the transmit axis in
  *    front).  Element type: MACH_IQ_C64 = interleaved float32 (re, im) ("complex64",
- *    Sec. 4.1); MACH_IQ_F16X2 = interleaved float16 (re, im), widened to float32 before
- *    any arithmetic.
+ *    Sec. 4.1); MACH_IQ_F16X2 / MACH_IQ_BF16X2 = interleaved float16 / bfloat16 (re, im),
+ *    widened to float32 before any arithmetic; MACH_IQ_C64_SPLIT = complex64 values with
+ *    every [sample] row stored as F real parts followed by F imaginary parts.
  *  - Output layout: y complex64 [n_vox][n_frames] (frames contiguous); Power Doppler
  *    float32 [n_vox].  Voxel order = the order of vox_pos, or for a regular grid
  *    v = ix + nx*(iy + ny*iz).
@@ -64,8 +65,19 @@ typedef enum {
 
 typedef enum {
     MACH_IQ_C64 = 0,     /* float32 (re, im) per sample, 8 bytes */
-    MACH_IQ_F16X2 = 1    /* float16 (re, im) per sample, 4 bytes */
+    MACH_IQ_F16X2 = 1,   /* float16 (re, im) per sample, 4 bytes */
+    MACH_IQ_BF16X2 = 2,  /* bfloat16 (re, im) per sample, 4 bytes */
+    MACH_IQ_C64_SPLIT = 3 /* complex64 with each sample row split: the n_frames real parts,
+                             then the n_frames imaginary parts (float32); n_frames a
+                             multiple of 4 and > 4.  Lets the kernels accumulate two frames
+                             per packed FP32x2 instruction */
 } mach_iq_dtype;
+
+/* Orders of channel data accepted by mach_iq_convert. */
+typedef enum {
+    MACH_ORDER_TCSF = 0,   /* [transmit][element][sample][frame]: the layout the kernels read */
+    MACH_ORDER_FTCS = 1    /* [frame][transmit][element][sample]: acquisition order          */
+} mach_iq_order;
 
 typedef struct mach_plan_s *mach_plan;
 
@@ -121,6 +133,16 @@ mach_status mach_das_run(mach_plan p, const void *iq_dev, void *y_dev, void *str
 mach_status mach_power_doppler(mach_plan p, const void *iq_dev, float *pd_dev,
                                void *y_dev_or_null, void *stream);
 
+/* Channel-data preparation (K0): read complex64 IQ in `src_order` and write it in the
+ * frame-contiguous layout [n_tx][n_elem][n_samples][n_frames] (Sec. 4.4's element,
+ * sample, frame order with the transmit axis in front) as `dst_dtype` (float16 and
+ * bfloat16 rounded to nearest even).  src_dev / dst_dev: distinct device buffers,
+ * 8- and 4-byte aligned.  Stream-ordered; a bandwidth-bound transpose through shared
+ * memory.  Errors: INVALID_ARG, UNSUPPORTED (grid limits), CUDA. */
+mach_status mach_iq_convert(const void *src_dev, int32_t src_order, void *dst_dev, int32_t dst_dtype,
+                            int32_t n_tx, int32_t n_elem, int32_t n_samples, int32_t n_frames,
+                            void *stream);
+
 /* Release a plan and its device tables (synchronises the device).  NULL is a no-op. */
 mach_status mach_plan_destroy(mach_plan p);
 
@@ -158,6 +180,52 @@ mach_status mach_plan_tx_table(mach_plan p, float *out_dev, void *stream);
  * vox_idx_dev: device int64 [n].  Any output may be NULL.  Stream-ordered. */
 mach_status mach_das_terms(mach_plan p, const int64_t *vox_idx_dev, int64_t n,
                            int32_t *i0_dev, float *w_dev, float *cw_dev, void *stream);
+
+/* ---- ragged batches ---------------------------------------------------------- */
+
+/* Lane mapping and voxel tile of one batch instance (chosen by an autotuner, or by
+ * mach_batch_plan when not given).  mode 0: frame lanes, `frame_lanes` (4, 8 or 16)
+ * lanes share a voxel and each holds 4 frames, so 4 * frame_lanes >= n_frames; one
+ * block covers 8 * 4 * (32 / frame_lanes) voxels.  mode 1: channel lanes (n_frames <= 4),
+ * 32 voxels per block.  tile: the block's voxel box (x, y, z); its volume must equal the
+ * block's voxel count (tile[1] = 1 in 2D), or all zero for the default box. */
+typedef struct {
+    int32_t mode;
+    int32_t frame_lanes;
+    int32_t tile[3];
+} mach_tile_shape;
+
+typedef struct mach_batch_s *mach_batch;
+
+/* Plan a batch of n instances (each described as for mach_das_plan, all with the same
+ * iq_dtype, not the split layout, n_frames <= 64): builds every instance's tables and one
+ * work list of (instance, voxel tile) items, sorted by decreasing estimated cost, for
+ * one persistent launch.  shapes: NULL or n entries.  Synchronises `stream`.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+mach_status mach_batch_plan(const mach_das_desc *descs, int32_t n, const mach_tile_shape *shapes,
+                            void *stream, mach_batch *out);
+
+/* Bind the device buffers of every instance (host arrays of n device pointers; per
+ * instance y or pd may be NULL but not both).  Uploads the instance table on `stream`;
+ * call again only when the buffers change. */
+mach_status mach_batch_bind(mach_batch b, const void *const *iq_devs, void *const *y_devs,
+                            float *const *pd_devs, void *stream);
+
+/* Beamform every instance of the batch in one launch on `stream` (stream-ordered; no
+ * host synchronisation, so it can be captured in a CUDA graph).  Runs on the same batch
+ * must be ordered on one stream (they share the work counter). */
+mach_status mach_batch_run(mach_batch b, void *stream);
+
+typedef struct {
+    int32_t instances;
+    int32_t items;           /* (instance, tile) work items                    */
+    int32_t blocks;          /* persistent blocks of one launch                */
+    int32_t blocks_per_sm;
+    int64_t points;          /* Eq. 1 points of one run (sum over instances)   */
+} mach_batch_info;
+
+mach_status mach_batch_get_info(mach_batch b, mach_batch_info *info, mach_tile_shape *shapes_or_null);
+mach_status mach_batch_destroy(mach_batch b);
 
 /* Synchronise `stream`, then report and clear the plan's device error word:
  * MACH_OK, or MACH_ERR_TIMEOUT when a bounded device-side wait of an earlier run on

@@ -98,7 +98,7 @@ def _iq_array(iq):
         import torch
         if isinstance(iq, torch.Tensor):
             iq = iq.detach().cpu()
-            if iq.dtype == torch.float16:           # f16x2 storage [...,2]
+            if iq.dtype in (torch.float16, torch.bfloat16):   # 16-bit pair storage [...,2]
                 iq = torch.view_as_complex(iq.float().contiguous())
             iq = iq.to(torch.complex64).numpy()
     except ImportError:

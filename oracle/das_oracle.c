@@ -38,9 +38,9 @@
  *                  fixed sequence: coordinates scaled by fs/c in FP64 then rounded to
  *                  float; s_tx = RN_float(fma(ux,px, fma(uy,py, uz*pz)) * fs/c - t0 fs)
  *                  in FP64; rx = sqrtf(fmaf(dx,dx, fmaf(dy,dy, dz*dz))); s = s_tx + rx;
- *                  i0 = floorf(s); w = s - i0; aperture test rho*2F# <= dz in float with
- *                  rho = sqrtf(fmaf(dx,dx, dy*dy)).  Everything after the index (window
- *                  value, phase, interpolation, sums) is FP64.
+ *                  i0 = floorf(s); w = s - i0; aperture test in float, squared:
+ *                  fmaf(dx,dx, dy*dy) * RN_float(4 F#^2) <= dz*dz (and dz > 0).  Everything
+ *                  after the index (window value, phase, interpolation, sums) is FP64.
  *
  * Build: gcc -O2 -ffp-contract=off -fopenmp -fPIC -shared  (no fast-math: the float
  * steps of the contract mode must round exactly as written).
@@ -162,11 +162,12 @@ static void make_term(const oracle_desc *d, int64_t v, int c, int t, const doubl
         float fdx = vx - ex, fdy = vy - ey, fdz = vz - ez;
         float rx = sqrtf(fmaf(fdx, fdx, fmaf(fdy, fdy, fdz * fdz)));
         float fs_ = tx_samples_contract(d, t, v, p) + rx;
-        float frho = sqrtf(fmaf(fdx, fdx, fdy * fdy));
-        float two_f = (float)(2.0 * d->f_number);
-        in_ap = (d->apod == OR_APOD_NONE) || (fdz > 0.0f && frho * two_f <= fdz);
+        /* aperture test squared (rho*2F# <= dz  <=>  rho^2 * 4F#^2 <= dz^2 for dz > 0) */
+        float frho2 = fmaf(fdx, fdx, fdy * fdy);
+        float four_f2 = (float)(4.0 * d->f_number * d->f_number);
+        in_ap = (d->apod == OR_APOD_NONE) || (fdz > 0.0f && frho2 * four_f2 <= fdz * fdz);
         s = (double)fs_;
-        rho = (double)frho;
+        rho = sqrt((double)frho2);
         dz = (double)fdz;
     }
     o->s = s;

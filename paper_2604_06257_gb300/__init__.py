@@ -24,13 +24,15 @@ LIB_PATH = os.path.join(_PKG, "libmach_gb300.so")
 
 MACH_OK, MACH_ERR_INVALID_ARG, MACH_ERR_CUDA, MACH_ERR_OOM, MACH_ERR_UNSUPPORTED, MACH_ERR_TIMEOUT = range(6)
 APOD = {"none": 0, "boxcar": 1, "hann": 2, "gauss": 3}
-IQ_DTYPE = {"c64": 0, "f16x2": 1}
+IQ_DTYPE = {"c64": 0, "f16x2": 1, "bf16x2": 2, "c64split": 3}
+ORDER = {"tcsf": 0, "ftcs": 1}
 
 EXPORTS = ("mach_das_plan", "mach_das_run", "mach_power_doppler", "mach_plan_destroy",
            "mach_status_string", "mach_plan_get_info", "mach_plan_tx_table", "mach_das_terms",
            "mach_version", "mach_debug_fail_alloc_after", "mach_plan_device_status",
            "mach_debug_force_variant", "mach_debug_set_wait_limit", "mach_debug_stall_producer",
-           "mach_das_run_noalloc")
+           "mach_das_run_noalloc", "mach_iq_convert", "mach_batch_plan", "mach_batch_bind",
+           "mach_batch_run", "mach_batch_get_info", "mach_batch_destroy")
 
 
 class MachError(RuntimeError):
@@ -69,6 +71,15 @@ class mach_plan_info(C.Structure):
                 "ring_slots": self.ring_slots, "copy_pairs": self.copy_pairs}
 
 
+class mach_tile_shape(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("frame_lanes", C.c_int32), ("tile", C.c_int32 * 3)]
+
+
+class mach_batch_info(C.Structure):
+    _fields_ = [("instances", C.c_int32), ("items", C.c_int32), ("blocks", C.c_int32),
+                ("blocks_per_sm", C.c_int32), ("points", C.c_int64)]
+
+
 _lib = None
 
 
@@ -102,6 +113,16 @@ def lib():
         L.mach_debug_stall_producer.argtypes = [i32]
         L.mach_debug_stall_producer.restype = None
         L.mach_das_run_noalloc.argtypes = [C.POINTER(mach_das_desc), vp, vp, vp, vp]
+        L.mach_iq_convert.argtypes = [vp, i32, vp, i32, i32, i32, i32, i32, vp]
+        L.mach_iq_convert.restype = C.c_int
+        L.mach_batch_plan.argtypes = [vp, i32, vp, vp, C.POINTER(vp)]
+        L.mach_batch_bind.argtypes = [vp, vp, vp, vp, vp]
+        L.mach_batch_run.argtypes = [vp, vp]
+        L.mach_batch_get_info.argtypes = [vp, C.POINTER(mach_batch_info), vp]
+        L.mach_batch_destroy.argtypes = [vp]
+        for f in ("mach_batch_plan", "mach_batch_bind", "mach_batch_run", "mach_batch_get_info",
+                  "mach_batch_destroy"):
+            getattr(L, f).restype = C.c_int
         L.mach_das_run_noalloc.restype = C.c_int
         for f in ("mach_das_plan", "mach_das_run", "mach_power_doppler", "mach_plan_destroy",
                   "mach_plan_get_info", "mach_plan_tx_table", "mach_das_terms"):
@@ -253,6 +274,33 @@ def mach_das_run_noalloc(desc, iq, y=None, pd=None, stream=None) -> None:
         raise MachError(st, "mach_das_run_noalloc")
 
 
+def mach_iq_convert(src, src_order, dst, dst_dtype, n_tx, n_elem, n_samples, n_frames, stream=None) -> None:
+    st = lib().mach_iq_convert(_dev_ptr(src, "src"), ORDER.get(src_order, src_order), _dev_ptr(dst, "dst"),
+                               IQ_DTYPE.get(dst_dtype, dst_dtype), int(n_tx), int(n_elem), int(n_samples),
+                               int(n_frames), _stream_ptr(stream))
+    if st != MACH_OK:
+        raise MachError(st, "mach_iq_convert")
+
+
+def prepare_iq(src, src_order="ftcs", dtype="c64", shape=None, stream=None):
+    """K0 on a complex64 CUDA tensor: returns the kernels' layout [T, C, S, F] (complex64),
+    [T, C, S, F, 2] (float16 / bfloat16) or [T, C, S, 2, F] (float32, split rows).  ``shape`` = (T, C, S, F); defaults from ``src``:
+    [F, T, C, S] for "ftcs", [T, C, S, F] for "tcsf"."""
+    import torch
+    if shape is None:
+        shape = (src.shape[1], src.shape[2], src.shape[3], src.shape[0]) if src_order == "ftcs" else tuple(src.shape)
+    T, Cn, S, F = shape
+    if dtype == "c64":
+        out = torch.empty((T, Cn, S, F), dtype=torch.complex64, device=src.device)
+    elif dtype == "c64split":
+        out = torch.empty((T, Cn, S, 2, F), dtype=torch.float32, device=src.device)
+    else:
+        out = torch.empty((T, Cn, S, F, 2), dtype=torch.float16 if dtype == "f16x2" else torch.bfloat16,
+                          device=src.device)
+    mach_iq_convert(src, src_order, out, dtype, T, Cn, S, F, stream)
+    return out
+
+
 def mach_plan_destroy(plan: int) -> None:
     st = lib().mach_plan_destroy(plan)
     if st != MACH_OK:
@@ -293,7 +341,7 @@ class Plan:
         self.desc, self._host = make_desc(**desc_kw)
         self.n_vox = int(self.desc.n_vox)
         self.n_frames = int(self.desc.n_frames)
-        self.iq_dtype = "f16x2" if self.desc.iq_dtype == 1 else "c64"
+        self.iq_dtype = {0: "c64", 1: "f16x2", 2: "bf16x2", 3: "c64split"}[int(self.desc.iq_dtype)]
         self.iq_shape = (int(self.desc.n_tx), int(self.desc.n_elem), int(self.desc.n_samples),
                          self.n_frames)
         self.handle = mach_das_plan(self.desc, stream)
@@ -330,9 +378,14 @@ class Plan:
         if self.iq_dtype == "c64":
             if iq.dtype != torch.complex64 or tuple(iq.shape) != self.iq_shape:
                 raise ValueError(f"iq must be complex64 {self.iq_shape}, got {iq.dtype} {tuple(iq.shape)}")
+        elif self.iq_dtype == "c64split":
+            T, Cn, S, F = self.iq_shape
+            if iq.dtype != torch.float32 or tuple(iq.shape) != (T, Cn, S, 2, F):
+                raise ValueError(f"iq must be float32 {(T, Cn, S, 2, F)} (split rows)")
         else:
-            if iq.dtype != torch.float16 or tuple(iq.shape) != self.iq_shape + (2,):
-                raise ValueError(f"iq must be float16 {self.iq_shape + (2,)}")
+            want = torch.float16 if self.iq_dtype == "f16x2" else torch.bfloat16
+            if iq.dtype != want or tuple(iq.shape) != self.iq_shape + (2,):
+                raise ValueError(f"iq must be {want} {self.iq_shape + (2,)}")
 
     def _buf(self, name, shape, dtype):
         torch = self._torch
@@ -414,6 +467,76 @@ class Plan:
         cw = torch.empty((n, Cn, T, 2), dtype=torch.float32, device="cuda")
         mach_das_terms(self.handle, idx, i0, w, cw)
         return i0, w, torch.view_as_complex(cw)
+
+
+# ---- ragged batches ------------------------------------------------------------------
+
+class Batch:
+    """Many instances (``plan_kwargs``-style dicts) beamformed by one persistent launch.
+    ``shapes``: optional list of (mode, frame_lanes, (tx, ty, tz)) per instance, e.g. from
+    ``autotune.tune_batch``; None uses the library's default lane mapping and tile box."""
+
+    def __init__(self, instances, shapes=None, stream=None):
+        self._descs_keep = [make_desc(**kw) for kw in instances]
+        n = len(instances)
+        arr = (mach_das_desc * n)(*[d for d, _ in self._descs_keep])
+        sh = None
+        if shapes is not None:
+            sh = (mach_tile_shape * n)()
+            for i, (mode, fl, tile) in enumerate(shapes):
+                sh[i].mode, sh[i].frame_lanes = int(mode), int(fl)
+                sh[i].tile = (C.c_int32 * 3)(*(tile if tile is not None else (0, 0, 0)))
+        h = C.c_void_p()
+        st = lib().mach_batch_plan(C.cast(arr, C.c_void_p), n, None if sh is None else C.cast(sh, C.c_void_p),
+                                   _stream_ptr(stream), C.byref(h))
+        if st != MACH_OK:
+            raise MachError(st, "mach_batch_plan")
+        self.handle = h.value
+        self.n = n
+        self.shapes_in = sh
+
+    def info(self) -> dict:
+        inf = mach_batch_info()
+        shp = (mach_tile_shape * self.n)()
+        st = lib().mach_batch_get_info(self.handle, C.byref(inf), C.cast(shp, C.c_void_p))
+        if st != MACH_OK:
+            raise MachError(st, "mach_batch_get_info")
+        return {"instances": inf.instances, "items": inf.items, "blocks": inf.blocks,
+                "blocks_per_sm": inf.blocks_per_sm, "points": inf.points,
+                "shapes": [(x.mode, x.frame_lanes, tuple(x.tile)) for x in shp]}
+
+    def bind(self, iqs, ys=None, pds=None, stream=None):
+        n = self.n
+        ia = (C.c_void_p * n)(*[_dev_ptr(t, "iq") for t in iqs])
+        ya = None if ys is None else (C.c_void_p * n)(*[_dev_ptr(t, "y") for t in ys])
+        pa = None if pds is None else (C.c_void_p * n)(*[_dev_ptr(t, "pd") for t in pds])
+        st = lib().mach_batch_bind(self.handle, C.cast(ia, C.c_void_p),
+                                   None if ya is None else C.cast(ya, C.c_void_p),
+                                   None if pa is None else C.cast(pa, C.c_void_p), _stream_ptr(stream))
+        if st != MACH_OK:
+            raise MachError(st, "mach_batch_bind")
+
+    def run(self, stream=None):
+        st = lib().mach_batch_run(self.handle, _stream_ptr(stream))
+        if st != MACH_OK:
+            raise MachError(st, "mach_batch_run")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().mach_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def plan_kwargs(acq) -> dict:

@@ -9,8 +9,9 @@
 //   i0  = floor(s), w = s - i0 (exact)            linear interpolation, Sec. 4.1
 // The window and phase are float32 approximations (errors ~1e-7, far below the
 // interpolation's own quantisation):
-//   aperture: rho = sqrt_rn(fma(dx,dx, dy*dy)); kept iff dz > 0 and rho*2F# <= dz;
-//             window of t = rho F#/dz: boxcar 1, Hann cos^2(pi t), Gaussian exp(-8 t^2)
+//   aperture: kept iff dz > 0 and fma(dx,dx, dy*dy) * RN(4F#^2) <= dz*dz (the test
+//             rho*2F# <= dz taken squared); window of t = rho F#/dz: boxcar 1,
+//             Hann cos^2(pi t), Gaussian exp(-8 t^2)
 //   phase:    fc (t0 + s/fs) cycles = frac(fc t0) + i0 frac(fc/fs) + w fc/fs, with the
 //             first two terms in 32-bit fixed point (exact wrap-around modulo one cycle)
 //             so that large sample indices lose no phase accuracy.
@@ -39,8 +40,9 @@ __device__ __forceinline__ TermGeo term_geometry(const float4 v, const float4 e,
     g.a = 1.0f;
     return g;
   }
-  const float rho = __fsqrt_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)));
-  if (!(dz > 0.0f && __fmul_rn(rho, p.two_f) <= dz)) {
+  // aperture test squared: rho^2 * 4F#^2 <= dz^2 (and dz > 0) -- no square root decides it
+  const float rho2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+  if (!(dz > 0.0f && __fmul_rn(rho2, p.four_f2) <= __fmul_rn(dz, dz))) {
     g.a = -1.0f;
     return g;
   }
@@ -48,12 +50,14 @@ __device__ __forceinline__ TermGeo term_geometry(const float4 v, const float4 e,
     g.a = 1.0f;
     return g;
   }
-  const float t = __fdividef(rho * p.f_num, dz);   // in [0, 1/2]
+  // window of t = rho F# / dz in [0, 1/2]; t^2 = rho^2 F#^2 / dz^2
+  const float t2 = __fdividef(rho2 * p.f_num2, dz * dz);
   if (p.apod == MACH_APOD_HANN) {
+    const float t = t2 > 0.0f ? t2 * rsqrtf(t2) : 0.0f;
     const float cp = __cosf(3.14159265358979f * t);
     g.a = cp * cp;
   } else {
-    g.a = __expf(-8.0f * t * t);
+    g.a = __expf(-8.0f * t2);
   }
   return g;
 }

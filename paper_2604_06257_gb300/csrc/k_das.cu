@@ -15,69 +15,27 @@
 // "Channel lanes" kernels (F <= 4): CL lanes share one voxel, lane j takes elements
 // j, j + CL, ...; each lane evaluates its own terms, and the partial sums are combined by
 // a shuffle tree (pairwise, so rounding grows with log CL).
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
 #include "das_term.cuh"
+#include "tap_mac.cuh"
 #include "mach_internal.h"
 
 namespace mach {
 
-// ---- IQ loads: VEC complex samples (widened to float2) from 16-byte vectors ---------
 template <class IQ, int VEC>
-struct IqVec;
-
-template <>
-struct IqVec<float2, 1> {
-  static __device__ __forceinline__ void load(const float2* p, float2 (&o)[1]) { o[0] = __ldg(p); }
-};
-template <>
-struct IqVec<float2, 2> {
-  static __device__ __forceinline__ void load(const float2* p, float2 (&o)[2]) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    o[0] = make_float2(v.x, v.y);
-    o[1] = make_float2(v.z, v.w);
-  }
-};
-template <>
-struct IqVec<__half2, 1> {
-  static __device__ __forceinline__ void load(const __half2* p, float2 (&o)[1]) {
-    o[0] = __half22float2(__ldg(p));
-  }
-};
-template <>
-struct IqVec<__half2, 4> {
-  static __device__ __forceinline__ void load(const __half2* p, float2 (&o)[4]) {
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
-    o[0] = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
-    o[1] = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
-    o[2] = __half22float2(*reinterpret_cast<const __half2*>(&v.z));
-    o[3] = __half22float2(*reinterpret_cast<const __half2*>(&v.w));
-  }
-};
-
-// acc += c0 * x0 + c1 * x1 (complex), c0 = (1 - w) c, c1 = w c.
-__device__ __forceinline__ void mac2(float2& acc, float c0r, float c0i, float c1r, float c1i,
-                                     float2 x0, float2 x1) {
-  acc.x = fmaf(c0r, x0.x, acc.x);
-  acc.x = fmaf(-c0i, x0.y, acc.x);
-  acc.x = fmaf(c1r, x1.x, acc.x);
-  acc.x = fmaf(-c1i, x1.y, acc.x);
-  acc.y = fmaf(c0r, x0.y, acc.y);
-  acc.y = fmaf(c0i, x0.x, acc.y);
-  acc.y = fmaf(c1r, x1.y, acc.y);
-  acc.y = fmaf(c1i, x1.x, acc.y);
-}
-
-template <int VEC>
-__device__ __forceinline__ void store_y(float2* dst, const float2* src) {
+__device__ __forceinline__ void store_y(float2* dst, const float2* acc_m) {
   if constexpr (VEC == 1) {
-    dst[0] = src[0];
+    dst[0] = acc_m[0];
   } else {
 #pragma unroll
-    for (int e = 0; e < VEC; e += 2)
-      *reinterpret_cast<float4*>(dst + e) = make_float4(src[e].x, src[e].y, src[e + 1].x, src[e + 1].y);
+    for (int e = 0; e < VEC; e += 2) {
+      const float2 a = acc_frame<IQ, VEC>(acc_m, e), b = acc_frame<IQ, VEC>(acc_m, e + 1);
+      *reinterpret_cast<float4*>(dst + e) = make_float4(a.x, a.y, b.x, b.y);
+    }
   }
 }
 
@@ -101,7 +59,9 @@ __global__ void __launch_bounds__(NWARP * 32) k_das_frames(const DasParams p) {
   const int jl = lane % FL;
   const int f_base = blockIdx.y * FT;
   const int64_t tile = blockIdx.x;
-  const IQ* __restrict__ iq = static_cast<const IQ*>(p.iq);
+  using E = typename IqStore<IQ>::E;
+  const E* __restrict__ iq = static_cast<const E*>(p.iq);
+  const int row_elems = p.F * IqStore<IQ>::eps;
 
   // the term this lane evaluates each round: voxel slot lane % WV, element cc + lane / WV
   const int64_t v_term = tile_voxel(p, tile, warp * WV + (lane % WV));
@@ -118,7 +78,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_das_frames(const DasParams p) {
 #pragma unroll
     for (int e = 0; e < FPL; ++e) acc[k][e] = make_float2(0.f, 0.f);
 
-  const size_t slab = static_cast<size_t>(p.S) * p.F;   // samples x frames per (t, c)
+  const size_t slab = static_cast<size_t>(p.S) * row_elems;   // samples x frames per (t, c)
   for (int cc = 0; cc < p.C; cc += CPR) {
     const int c = cc + c_sub;
     TermGeo geo;
@@ -139,7 +99,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_das_frames(const DasParams p) {
         for (int j = 0; j < CPR; ++j) {
           const int c2 = cc + j;
           if (c2 >= p.C) break;
-          const IQ* base = iq + (static_cast<size_t>(tb + tt) * p.C + c2) * slab;
+          const E* base = iq + (static_cast<size_t>(tb + tt) * p.C + c2) * slab;
 #pragma unroll
           for (int k = 0; k < VPG; ++k) {
             const float4 r = terms[tt * 32 + j * WV + k * G + g];
@@ -147,18 +107,8 @@ __global__ void __launch_bounds__(NWARP * 32) k_das_frames(const DasParams p) {
             if (i0 >= 0) {
               const float c1r = r.x * r.z, c1i = r.y * r.z;
               const float c0r = r.x - c1r, c0i = r.y - c1i;
-              const IQ* row0 = base + static_cast<size_t>(i0) * p.F;
-#pragma unroll
-              for (int m = 0; m < NV; ++m) {
-                const int f = f_base + (jl + FL * m) * VEC;
-                if (f < p.F) {
-                  float2 x0[VEC], x1[VEC];
-                  IqVec<IQ, VEC>::load(row0 + f, x0);
-                  IqVec<IQ, VEC>::load(row0 + p.F + f, x1);
-#pragma unroll
-                  for (int e = 0; e < VEC; ++e) mac2(acc[k][m * VEC + e], c0r, c0i, c1r, c1i, x0[e], x1[e]);
-                }
-              }
+              gather_mac<IQ, VEC, NV, FL, false>(acc[k], base + static_cast<size_t>(i0) * row_elems, row_elems, p.F,
+                                                 f_base, jl, c0r, c0i, c1r, c1i);
             }
           }
         }
@@ -177,10 +127,10 @@ __global__ void __launch_bounds__(NWARP * 32) k_das_frames(const DasParams p) {
       if (f < p.F) {
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
-          const float2 a = acc[k][m * VEC + e];
+          const float2 a = acc_frame<IQ, VEC>(&acc[k][m * VEC], e);
           pw = fmaf(a.x, a.x, fmaf(a.y, a.y, pw));
         }
-        if (v >= 0 && p.y) store_y<VEC>(p.y + v * p.F + f, &acc[k][m * VEC]);
+        if (v >= 0 && p.y) store_y<IQ, VEC>(p.y + v * p.F + f, &acc[k][m * VEC]);
       }
     }
 #pragma unroll
@@ -223,9 +173,9 @@ __global__ void __launch_bounds__(NWARP * 32) k_das_channels(const DasParams p) 
         for (int f = 0; f < FMAX; ++f) {
           if (f < p.F) {
             float2 x0[1], x1[1];
-            IqVec<IQ, 1>::load(row0 + f, x0);
-            IqVec<IQ, 1>::load(row0 + p.F + f, x1);
-            mac2(acc[f], c0r, c0i, c1r, c1i, x0[0], x1[0]);
+            load_vec<IQ, 1, false>(row0 + f, x0);
+            load_vec<IQ, 1, false>(row0 + p.F + f, x1);
+            mac1(acc[f], c0r, c0i, c1r, c1i, x0[0], x1[0]);
           }
         }
       }
@@ -266,21 +216,37 @@ namespace {
 constexpr int kWarps = 8;
 //                          name                FPL  lanes vox/warp  FT  warps  ch-lanes
 const VariantShape kShapes[V_COUNT] = {
-    //  name                      FPL lanes vox/warp FT  warps ch-lanes staged ring bytes
-    {"channels_c64_cl8",           1,  8,   4,    4,  kWarps, true,  false, 0, 8},
-    {"frames_c64_ft16",            2,  8,  32,   16,  kWarps, false, false, 0, 8},
-    {"frames_c64_ft32",            4,  8,  32,   32,  kWarps, false, false, 0, 8},
-    {"frames_c64_ft64",            4, 16,  16,   64,  kWarps, false, false, 0, 8},
-    {"frames_c64_scalar_ft32",     1, 32,  16,   32,  kWarps, false, false, 0, 8},
-    {"channels_f16_cl8",           1,  8,   4,    4,  kWarps, true,  false, 0, 4},
-    {"frames_f16_ft32",            4,  8,  32,   32,  kWarps, false, false, 0, 4},
-    {"frames_f16_ft64",            4, 16,  16,   64,  kWarps, false, false, 0, 4},
-    {"frames_f16_scalar_ft32",     1, 32,  16,   32,  kWarps, false, false, 0, 4},
-    {"staged_c64_ft32",            4,  8,  32,   32,  kWarps, false, true,  4, 8},
-    {"staged_c64_ft64",            4, 16,  16,   64,  kWarps, false, true,  4, 8},
-    {"staged_f16_ft32",            4,  8,  32,   32,  kWarps, false, true,  4, 4},
-    {"staged_f16_ft64",            4, 16,  16,   64,  kWarps, false, true,  4, 4},
-    {"staged_c64_ft32_v4",         4,  8,  16,   32,  kWarps, false, true,  4, 8},
+    //  name                      FPL lanes vox/warp FT  warps ch-lanes staged ring bytes type
+    {"channels_c64_cl8",           1,  8,   4,    4,  kWarps, true,  false, 0, 8, 0},
+    {"frames_c64_ft16",            2,  8,  32,   16,  kWarps, false, false, 0, 8, 0},
+    {"frames_c64_ft32",            4,  8,  32,   32,  kWarps, false, false, 0, 8, 0},
+    {"frames_c64_ft64",            4, 16,  16,   64,  kWarps, false, false, 0, 8, 0},
+    {"frames_c64_scalar_ft32",     1, 32,  16,   32,  kWarps, false, false, 0, 8, 0},
+    {"channels_f16_cl8",           1,  8,   4,    4,  kWarps, true,  false, 0, 4, 1},
+    {"frames_f16_ft32",            4,  8,  32,   32,  kWarps, false, false, 0, 4, 1},
+    {"frames_f16_ft64",            4, 16,  16,   64,  kWarps, false, false, 0, 4, 1},
+    {"frames_f16_scalar_ft32",     1, 32,  16,   32,  kWarps, false, false, 0, 4, 1},
+    {"staged_c64_ft32",            4,  8,  32,   32,  kWarps, false, true,  4, 8, 0},
+    {"staged_c64_ft64",            4, 16,  16,   64,  kWarps, false, true,  4, 8, 0},
+    {"staged_f16_ft32",            4,  8,  32,   32,  kWarps, false, true,  4, 4, 1},
+    {"staged_f16_ft64",            4, 16,  16,   64,  kWarps, false, true,  4, 4, 1},
+    {"staged_c64_ft32_v4",         4,  8,  16,   32,  kWarps, false, true,  4, 8, 0},
+    {"staged_c64_ft32_v4w4",       4,  8,  16,   32,  4,      false, true,  4, 8, 0},
+    {"staged_c64_ft64_v4",         4, 16,   8,   64,  kWarps, false, true,  8, 8, 0},
+    {"staged_f16_ft64_v4",         4, 16,   8,   64,  kWarps, false, true,  8, 4, 1},
+    {"channels_b16_cl8",           1,  8,   4,    4,  kWarps, true,  false, 0, 4, 2},
+    {"frames_b16_ft32",            4,  8,  32,   32,  kWarps, false, false, 0, 4, 2},
+    {"frames_b16_ft64",            4, 16,  16,   64,  kWarps, false, false, 0, 4, 2},
+    {"frames_b16_scalar_ft32",     1, 32,  16,   32,  kWarps, false, false, 0, 4, 2},
+    {"staged_b16_ft32",            4,  8,  32,   32,  kWarps, false, true,  4, 4, 2},
+    {"staged_b16_ft64_v4",         4, 16,   8,   64,  kWarps, false, true,  8, 4, 2},
+    {"staged_c64_ft32_v4r56",      4,  8,  16,   32,  kWarps, false, true,  4, 8, 0},
+    {"frames_c64p_ft32",           4,  8,  32,   32,  kWarps, false, false, 0, 8, 3},
+    {"frames_c64p_ft64",           4, 16,  16,   64,  kWarps, false, false, 0, 8, 3},
+    {"staged_c64p_ft32_v4",        4,  8,  16,   32,  kWarps, false, true,  4, 8, 3},
+    {"staged_c64p_ft64_v4",        4, 16,   8,   64,  kWarps, false, true,  8, 8, 3},
+    {"staged_f16_ft32_v4",         4,  8,  16,   32,  kWarps, false, true,  4, 4, 1},
+    {"staged_b16_ft32_v4",         4,  8,  16,   32,  kWarps, false, true,  4, 4, 2},
 };
 
 template <class K>
@@ -312,6 +278,12 @@ cudaError_t launch_das(const DasParams& p, Variant v, cudaStream_t s) {
     case V_F32_H16: e = go(k_das_frames<__half2, 4, 1, 8, 8, kWarps>, p, sm, s); break;
     case V_F64_H16: e = go(k_das_frames<__half2, 4, 1, 16, 8, kWarps>, p, sm, s); break;
     case V_S32_H16: e = go(k_das_frames<__half2, 1, 1, 32, 16, kWarps>, p, sm, s); break;
+    case V_CH_B16: e = go(k_das_channels<__nv_bfloat162, 8, 4, kWarps>, p, sm, s); break;
+    case V_F32_B16: e = go(k_das_frames<__nv_bfloat162, 4, 1, 8, 8, kWarps>, p, sm, s); break;
+    case V_F64_B16: e = go(k_das_frames<__nv_bfloat162, 4, 1, 16, 8, kWarps>, p, sm, s); break;
+    case V_S32_B16: e = go(k_das_frames<__nv_bfloat162, 1, 1, 32, 16, kWarps>, p, sm, s); break;
+    case V_F32_C64P: e = go(k_das_frames<C64Planar, 4, 1, 8, 8, kWarps>, p, sm, s); break;
+    case V_F64_C64P: e = go(k_das_frames<C64Planar, 4, 1, 16, 8, kWarps>, p, sm, s); break;
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;

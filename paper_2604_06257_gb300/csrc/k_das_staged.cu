@@ -14,12 +14,14 @@
 // Synchronisation: per slot a "full" mbarrier (producer arrival + transaction bytes)
 // and an "empty" mbarrier (one arrival per consumer warp).  Every wait is bounded; on a
 // timeout the kernel sets bit 0 of the plan's error word and returns.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
 #include "async_copy.cuh"
 #include "das_term.cuh"
+#include "tap_mac.cuh"
 #include "mach_internal.h"
 
 namespace mach {
@@ -115,59 +117,6 @@ cudaError_t launch_tile_bounds(const DasParams& p, float4* tbox, float2* txr, in
   return cudaGetLastError();
 }
 
-// ---- shared-memory tap loads ------------------------------------------------------------
-template <class IQ, int VEC>
-struct SmemVec;
-template <>
-struct SmemVec<float2, 2> {
-  static __device__ __forceinline__ void load(const float2* p, float2 (&o)[2]) {
-    const float4 v = *reinterpret_cast<const float4*>(p);
-    o[0] = make_float2(v.x, v.y);
-    o[1] = make_float2(v.z, v.w);
-  }
-};
-template <>
-struct SmemVec<__half2, 4> {
-  static __device__ __forceinline__ void load(const __half2* p, float2 (&o)[4]) {
-    const uint4 v = *reinterpret_cast<const uint4*>(p);
-    o[0] = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
-    o[1] = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
-    o[2] = __half22float2(*reinterpret_cast<const __half2*>(&v.z));
-    o[3] = __half22float2(*reinterpret_cast<const __half2*>(&v.w));
-  }
-};
-template <class IQ, int VEC>
-struct GlobVec;
-template <>
-struct GlobVec<float2, 2> {
-  static __device__ __forceinline__ void load(const float2* p, float2 (&o)[2]) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    o[0] = make_float2(v.x, v.y);
-    o[1] = make_float2(v.z, v.w);
-  }
-};
-template <>
-struct GlobVec<__half2, 4> {
-  static __device__ __forceinline__ void load(const __half2* p, float2 (&o)[4]) {
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
-    o[0] = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
-    o[1] = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
-    o[2] = __half22float2(*reinterpret_cast<const __half2*>(&v.z));
-    o[3] = __half22float2(*reinterpret_cast<const __half2*>(&v.w));
-  }
-};
-
-__device__ __forceinline__ void mac_st(float2& acc, float c0r, float c0i, float c1r, float c1i, float2 x0, float2 x1) {
-  acc.x = fmaf(c0r, x0.x, acc.x);
-  acc.x = fmaf(-c0i, x0.y, acc.x);
-  acc.x = fmaf(c1r, x1.x, acc.x);
-  acc.x = fmaf(-c1i, x1.y, acc.x);
-  acc.y = fmaf(c0r, x0.y, acc.y);
-  acc.y = fmaf(c0i, x0.x, acc.y);
-  acc.y = fmaf(c1r, x1.y, acc.y);
-  acc.y = fmaf(c1i, x1.x, acc.y);
-}
-
 // ---- the staged kernel --------------------------------------------------------------------
 constexpr int kTxCache = 16;   // transmits whose delays are cached in shared memory per warp
 
@@ -191,50 +140,34 @@ struct SlotMeta {
   float4 e;             // element position (sample units)
 };
 
-template <class IQ, int VEC, int NV, int FL>
-__device__ __forceinline__ void gather_mac(float2 (&acc)[VEC * NV], const IQ* r0, int F, int f_base, int jl,
-                                           float c0r, float c0i, float c1r, float c1i, bool smem) {
-#pragma unroll
-  for (int mm = 0; mm < NV; ++mm) {
-    const int f = f_base + (jl + FL * mm) * VEC;
-    if (f < F) {
-      float2 x0[VEC], x1[VEC];
-      if (smem) {
-        SmemVec<IQ, VEC>::load(r0 + f, x0);
-        SmemVec<IQ, VEC>::load(r0 + F + f, x1);
-      } else {
-        GlobVec<IQ, VEC>::load(r0 + f, x0);
-        GlobVec<IQ, VEC>::load(r0 + F + f, x1);
-      }
-#pragma unroll
-      for (int e = 0; e < VEC; ++e) mac_st(acc[mm * VEC + e], c0r, c0i, c1r, c1i, x0[e], x1[e]);
-    }
-  }
-}
-
 template <class IQ, int VEC, int NV, int FL, int VPG, int NWC, int NBUF, int MINB>
-__global__ void __launch_bounds__((NWC + 1) * 32) __maxnreg__(MINB == 2 ? 112 : (MINB == 3 ? 72 : 168)) k_das_staged(const DasParams p) {
+__global__ void __launch_bounds__((NWC + 1) * 32) __maxnreg__(MINB == 2 ? 112 : (MINB == 3 ? 72 : (MINB == 4 ? 56 : (MINB == 5 ? 80 : 168)))) k_das_staged(const DasParams p) {
   constexpr int G = 32 / FL;
   constexpr int WV = G * VPG;
   constexpr int FPL = VEC * NV;
   constexpr int FT = FL * FPL;
-  static_assert(WV <= 32, "one term per lane and pair");
+  constexpr int PB = 32 / WV;          // pairs whose terms one warp evaluates per round
+  static_assert(WV * PB == 32, "a round must fill the warp");
+  static_assert(NBUF >= PB, "a round must fit in the ring");
   extern __shared__ __align__(128) unsigned char smem[];
-  const RingLayout<NBUF> L(p.rows_cap, p.F, static_cast<int>(sizeof(IQ)), p.T, NWC);
-  IQ* ring = reinterpret_cast<IQ*>(smem);
+  using E = typename IqStore<IQ>::E;
+  constexpr int kBytes = static_cast<int>(sizeof(E)) * IqStore<IQ>::eps;   // bytes per complex sample
+  const RingLayout<NBUF> L(p.rows_cap, p.F, kBytes, p.T, NWC);
+  E* ring = reinterpret_cast<E*>(smem);
   float4* terms_all = reinterpret_cast<float4*>(smem + L.terms_off());
   float* txc_all = reinterpret_cast<float*>(smem + L.tx_off(NWC));
   SlotMeta* meta = reinterpret_cast<SlotMeta*>(smem + L.meta_off(NWC));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bar_off(NWC));
   uint64_t* empty = full + NBUF;
-  const size_t slot_elems = L.slot_bytes / sizeof(IQ);
+  const size_t slot_elems = L.slot_bytes / sizeof(E);
+  const int row_elems = p.F * IqStore<IQ>::eps;     // one sample row, all frames
   const bool tx_cached = p.T <= kTxCache;
 
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int64_t tile = blockIdx.x;
-  const IQ* __restrict__ iq = static_cast<const IQ*>(p.iq);
-  const size_t slab = static_cast<size_t>(p.S) * p.F;
+  const E* __restrict__ iq = static_cast<const E*>(p.iq);
+  const size_t slab = static_cast<size_t>(p.S) * row_elems;
 
   if (threadIdx.x == 0) {
     for (int b = 0; b < NBUF; ++b) {
@@ -246,41 +179,68 @@ __global__ void __launch_bounds__((NWC + 1) * 32) __maxnreg__(MINB == 2 ? 112 : 
   __syncthreads();
 
   // ------------------------------------------------------------------ producer
+  // The producer warp evaluates 32 (element, transmit) pairs at a time (one lane each,
+  // loads issued together), then lane 0 issues the copies of the usable ones in order.
   if (warp == NWC) {
-    if (lane != 0) return;
     const float4 blo = p.tbox[2 * tile], bhi = p.tbox[2 * tile + 1];
+    const int npairs = p.C * p.T;
     int r = 0;
     bool ok = true;
-    for (int c = 0; c < p.C && ok; ++c) {
-      const float4 e = __ldg(&p.elem[c]);
-      for (int t = 0; t < p.T; ++t) {
-        int lo, rows;
-        if (!pair_window(blo, bhi, p.txr[tile * p.T + t], e, p, lo, rows)) continue;
+    for (int pb = 0; pb < npairs && ok; pb += 32) {
+      const int pi = pb + lane;
+      int t = 0, c = 0, lo = 0, rows = 0;
+      float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+      bool use = false;
+      if (pi < npairs) {
+        c = pi / p.T;
+        t = pi - c * p.T;
+        e = __ldg(&p.elem[c]);
+        use = pair_window(blo, bhi, __ldg(&p.txr[tile * p.T + t]), e, p, lo, rows);
         rows = min(rows, p.rows_cap);
-        const int slot = r % NBUF;
-        if (r >= NBUF && !mbar_wait_bounded(&empty[slot], ((r / NBUF) - 1) & 1, p.wait_limit)) {
-          atomicOr(p.err, 1);
-          ok = false;
-          break;
+      }
+      unsigned todo = __ballot_sync(0xffffffffu, use);
+      while (todo) {
+        const int j = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int tj = __shfl_sync(0xffffffffu, t, j), cj = __shfl_sync(0xffffffffu, c, j);
+        const int loj = __shfl_sync(0xffffffffu, lo, j), rowsj = __shfl_sync(0xffffffffu, rows, j);
+        float4 ej;
+        ej.x = __shfl_sync(0xffffffffu, e.x, j);
+        ej.y = __shfl_sync(0xffffffffu, e.y, j);
+        ej.z = __shfl_sync(0xffffffffu, e.z, j);
+        ej.w = 0.f;
+        if (lane == 0) {
+          const int slot = r % NBUF;
+          if (r >= NBUF && !mbar_wait_bounded(&empty[slot], ((r / NBUF) - 1) & 1, p.wait_limit)) {
+            atomicOr(p.err, 1);
+            ok = false;
+          } else {
+            meta[slot].t = tj;
+            meta[slot].c = cj;
+            meta[slot].lo = loj;
+            meta[slot].rows = rowsj;
+            meta[slot].e = ej;
+            const uint32_t bytes = static_cast<uint32_t>(rowsj) * p.F * kBytes;
+            mbar_arrive_expect_tx(&full[slot], bytes);
+            if (!p.debug_stall)
+              bulk_g2s(ring + slot * slot_elems,
+                       iq + (static_cast<size_t>(tj) * p.C + cj) * slab + static_cast<size_t>(loj) * row_elems, bytes,
+                       &full[slot]);
+          }
         }
-        meta[slot].t = t;
-        meta[slot].c = c;
-        meta[slot].lo = lo;
-        meta[slot].rows = rows;
-        meta[slot].e = e;
-        const uint32_t bytes = static_cast<uint32_t>(rows) * p.F * sizeof(IQ);
-        mbar_arrive_expect_tx(&full[slot], bytes);
-        if (!p.debug_stall)
-          bulk_g2s(ring + slot * slot_elems, iq + (static_cast<size_t>(t) * p.C + c) * slab + static_cast<size_t>(lo) * p.F,
-                   bytes, &full[slot]);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
         ++r;
       }
     }
-    if (ok) {   // end-of-sequence marker
-      const int slot = r % NBUF;
-      if (r >= NBUF && !mbar_wait_bounded(&empty[slot], ((r / NBUF) - 1) & 1, p.wait_limit)) {
-        atomicOr(p.err, 1);
-      } else {
+    if (lane != 0) return;
+    if (ok) {   // one end-of-sequence marker per pair a consumer round can hold
+      for (int k = 0; k < PB; ++k) {
+        const int rr = r + k, slot = rr % NBUF;
+        if (rr >= NBUF && !mbar_wait_bounded(&empty[slot], ((rr / NBUF) - 1) & 1, p.wait_limit)) {
+          atomicOr(p.err, 1);
+          break;
+        }
         meta[slot].c = -1;
         mbar_arrive(&full[slot]);
       }
@@ -291,16 +251,21 @@ __global__ void __launch_bounds__((NWC + 1) * 32) __maxnreg__(MINB == 2 ? 112 : 
   }
 
   // ------------------------------------------------------------------ consumers
+  // Each round the warp takes PB consecutive pairs: lane group `sub` (WV lanes) evaluates
+  // the terms of pair r + sub for the warp's WV voxels, then the warp consumes the PB
+  // pairs one after the other.
   const int g = lane / FL;
   const int jl = lane % FL;
+  const int sub = lane / WV;
+  const int q = lane % WV;
   const int f_base = blockIdx.y * FT;
   float4* terms = terms_all + warp * 32;
   float* txc = txc_all + warp * (p.T * 32);
-  // lane < WV evaluates the terms of voxel slot `lane`; they are stored at k*G + g so
-  // that the G groups of the warp read G consecutive entries (no bank conflict)
-  const int64_t v_term = lane < WV ? tile_voxel_blocked(p, tile, warp * WV + lane) : -1;
+  // terms of voxel slot q for pair `sub` are stored at sub*WV + k*G + g (slot q = g*VPG + k),
+  // so the G groups of the warp read G consecutive entries (no bank conflict)
+  const int64_t v_term = tile_voxel_blocked(p, tile, warp * WV + q);
   const float4 vpos = v_term >= 0 ? p.vox[v_term] : make_float4(0.f, 0.f, 0.f, 0.f);
-  const int store_at = (lane % VPG) * G + (lane / VPG);
+  const int store_at = sub * WV + (q % VPG) * G + (q / VPG);
   if (tx_cached) {
     for (int t = 0; t < p.T; ++t) txc[t * 32 + lane] = v_term >= 0 ? p.tx[static_cast<size_t>(t) * p.V + v_term] : 0.f;
   }
@@ -315,69 +280,85 @@ __global__ void __launch_bounds__((NWC + 1) * 32) __maxnreg__(MINB == 2 ? 112 : 
   TermGeo geo;
   geo.rx = 0.f;
   geo.a = -1.f;
-  bool ok = true;
-  for (int r = 0;; ++r) {
-    const int slot = r % NBUF;
-    if (!mbar_wait_bounded(&full[slot], (r / NBUF) & 1, p.wait_limit)) {
+  bool ok = true, done = false;
+  for (int r = 0; !done; r += PB) {
+    const int mine = r + sub, my_slot = mine % NBUF;
+    const bool got = mbar_wait_bounded(&full[my_slot], (mine / NBUF) & 1, p.wait_limit);
+    if (__any_sync(0xffffffffu, !got)) {
       if (lane == 0) atomicOr(p.err, 1);
       ok = false;
       break;
     }
-    const SlotMeta m = meta[slot];
-    if (m.c < 0) break;
-    if (m.c != cur_c) {
-      cur_c = m.c;
-      geo.a = -1.f;
-      if (v_term >= 0) geo = term_geometry(vpos, m.e, p);
-    }
+    const SlotMeta mm = meta[my_slot];
     float4 rec = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
-    if (geo.a >= 0.f) {
-      const float stx = tx_cached ? txc[m.t * 32 + lane] : __ldg(&p.tx[static_cast<size_t>(m.t) * p.V + v_term]);
-      rec = term_record(stx, geo, p);
+    if (mm.c >= 0) {
+      if (mm.c != cur_c) {
+        cur_c = mm.c;
+        geo.a = -1.f;
+        if (v_term >= 0) geo = term_geometry(vpos, mm.e, p);
+      }
+      if (geo.a >= 0.f) {
+        const float stx = tx_cached ? txc[mm.t * 32 + lane] : __ldg(&p.tx[static_cast<size_t>(mm.t) * p.V + v_term]);
+        rec = term_record(stx, geo, p);
+      }
     }
     const int my_i0 = __float_as_int(rec.w);
     const bool active = my_i0 >= 0;
-    const bool outside = active && (my_i0 - m.lo < 0 || my_i0 - m.lo + 1 >= m.rows);
-    const unsigned any_active = __ballot_sync(0xffffffffu, active);
-    const unsigned any_outside = __ballot_sync(0xffffffffu, outside);
-    if (any_active) {
-      if (lane < WV) terms[store_at] = rec;
-      __syncwarp();
-      const IQ* win = ring + slot * slot_elems;
-      if (!any_outside) {
+    const bool outside = active && (my_i0 - mm.lo < 0 || my_i0 - mm.lo + 1 >= mm.rows);
+    const unsigned act = __ballot_sync(0xffffffffu, active);
+    const unsigned outm = __ballot_sync(0xffffffffu, outside);
+    const unsigned ended = __ballot_sync(0xffffffffu, mm.c < 0);
+    terms[store_at] = rec;
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < PB; ++i) {
+      const unsigned gm = WV == 32 ? 0xffffffffu : (((1u << (WV & 31)) - 1u) << (i * WV));
+      if (ended & gm) {   // end marker: every later pair of the round is one too
+        done = true;
+        break;
+      }
+      if (!(act & gm)) continue;
+      const int slot = (r + i) % NBUF;
+      const int lo = meta[slot].lo, rows = meta[slot].rows;
+      const E* win = ring + slot * slot_elems;
+      const float4* tp = terms + i * WV;
+      if (!(outm & gm)) {
         // every kept term lies in the staged window: branch-free over the voxels
         // (dropped terms carry zero weights and read row 0)
 #pragma unroll
         for (int k = 0; k < VPG; ++k) {
-          const float4 tr = terms[k * G + g];
-          const int row = max(__float_as_int(tr.w) - m.lo, 0);
+          const float4 tr = tp[k * G + g];
+          const int row = max(__float_as_int(tr.w) - lo, 0);
           const float c1r = tr.x * tr.z, c1i = tr.y * tr.z;
           const float c0r = tr.x - c1r, c0i = tr.y - c1i;
-          gather_mac<IQ, VEC, NV, FL>(acc[k], win + row * p.F, p.F, f_base, jl, c0r, c0i, c1r, c1i, true);
+          gather_mac<IQ, VEC, NV, FL, true>(acc[k], win + row * row_elems, row_elems, p.F, f_base, jl, c0r, c0i, c1r,
+                                            c1i);
         }
       } else {
         // some kept term falls outside the staged window (not expected): per-term
         // choice between the window and global memory
-        const IQ* gsrc = iq + (static_cast<size_t>(m.t) * p.C + m.c) * slab;
+        const int t = meta[slot].t, c = meta[slot].c;
+        const E* gsrc = iq + (static_cast<size_t>(t) * p.C + c) * slab;
 #pragma unroll
         for (int k = 0; k < VPG; ++k) {
-          const float4 tr = terms[k * G + g];
+          const float4 tr = tp[k * G + g];
           const int i0 = __float_as_int(tr.w);
           if (i0 >= 0) {
             const float c1r = tr.x * tr.z, c1i = tr.y * tr.z;
             const float c0r = tr.x - c1r, c0i = tr.y - c1i;
-            const int row = i0 - m.lo;
-            if (row >= 0 && row + 1 < m.rows)
-              gather_mac<IQ, VEC, NV, FL>(acc[k], win + row * p.F, p.F, f_base, jl, c0r, c0i, c1r, c1i, true);
+            const int row = i0 - lo;
+            if (row >= 0 && row + 1 < rows)
+              gather_mac<IQ, VEC, NV, FL, true>(acc[k], win + row * row_elems, row_elems, p.F, f_base, jl, c0r, c0i,
+                                                c1r, c1i);
             else
-              gather_mac<IQ, VEC, NV, FL>(acc[k], gsrc + static_cast<size_t>(i0) * p.F, p.F, f_base, jl, c0r, c0i,
-                                          c1r, c1i, false);
+              gather_mac<IQ, VEC, NV, FL, false>(acc[k], gsrc + static_cast<size_t>(i0) * row_elems, row_elems, p.F,
+                                                 f_base, jl, c0r, c0i, c1r, c1i);
           }
         }
       }
     }
     __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[slot]);
+    if (lane < PB) mbar_arrive(&empty[(r + lane) % NBUF]);
   }
   if (!ok) return;
 
@@ -391,16 +372,16 @@ __global__ void __launch_bounds__((NWC + 1) * 32) __maxnreg__(MINB == 2 ? 112 : 
       if (f < p.F) {
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
-          const float2 a = acc[k][mm * VEC + e];
+          const float2 a = acc_frame<IQ, VEC>(&acc[k][mm * VEC], e);
           pw = fmaf(a.x, a.x, fmaf(a.y, a.y, pw));
         }
         if (v >= 0 && p.y) {
           float2* dst = p.y + v * p.F + f;
 #pragma unroll
-          for (int e = 0; e < VEC; e += 2)
-            *reinterpret_cast<float4*>(dst + e) =
-                make_float4(acc[k][mm * VEC + e].x, acc[k][mm * VEC + e].y, acc[k][mm * VEC + e + 1].x,
-                            acc[k][mm * VEC + e + 1].y);
+          for (int e = 0; e < VEC; e += 2) {
+            const float2 a = acc_frame<IQ, VEC>(&acc[k][mm * VEC], e), b = acc_frame<IQ, VEC>(&acc[k][mm * VEC], e + 1);
+            *reinterpret_cast<float4*>(dst + e) = make_float4(a.x, a.y, b.x, b.y);
+          }
         }
       }
     }
@@ -412,32 +393,42 @@ __global__ void __launch_bounds__((NWC + 1) * 32) __maxnreg__(MINB == 2 ? 112 : 
 
 // ---- dispatch ------------------------------------------------------------------------------
 namespace {
-constexpr int kNWC = 8;     // consumer warps
-constexpr int kRing = 4;    // ring slots
+constexpr int kRing = 4;    // ring slots (8 when a round holds 4 pairs)
 
 template <class K>
-cudaError_t go_staged(K kernel, const DasParams& p, size_t smem, cudaStream_t s) {
+cudaError_t go_staged(K kernel, int nwc, const DasParams& p, size_t smem, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const int64_t tiles = static_cast<int64_t>(p.tiles_x) * p.tiles_y * p.tiles_z;
-  kernel<<<dim3(static_cast<unsigned>(tiles), 1), (kNWC + 1) * 32, smem, s>>>(p);
+  kernel<<<dim3(static_cast<unsigned>(tiles), 1), (nwc + 1) * 32, smem, s>>>(p);
   return cudaGetLastError();
 }
 }  // namespace
 
 size_t staged_smem_bytes(Variant v, int rows_cap, int F, int T) {
-  const int b = (v == V_ST32_H16 || v == V_ST64_H16) ? 4 : 8;
-  return RingLayout<kRing>(rows_cap, F, b, T, kNWC).total(kNWC);
+  const VariantShape& sh = variant_shape(v);
+  if (sh.ring_slots == 8) return RingLayout<8>(rows_cap, F, sh.iq_bytes, T, sh.warps).total(sh.warps);
+  return RingLayout<kRing>(rows_cap, F, sh.iq_bytes, T, sh.warps).total(sh.warps);
 }
 
 cudaError_t launch_das_staged(const DasParams& p, Variant v, cudaStream_t s) {
   const size_t sm = staged_smem_bytes(v, p.rows_cap, p.F, p.T);
   switch (v) {
-    case V_ST32_C64: return go_staged(k_das_staged<float2, 2, 2, 8, 8, kNWC, kRing, 2>, p, sm, s);
-    case V_ST64_C64: return go_staged(k_das_staged<float2, 2, 2, 16, 8, kNWC, kRing, 2>, p, sm, s);
-    case V_ST32_H16: return go_staged(k_das_staged<__half2, 4, 1, 8, 8, kNWC, kRing, 2>, p, sm, s);
-    case V_ST64_H16: return go_staged(k_das_staged<__half2, 4, 1, 16, 8, kNWC, kRing, 2>, p, sm, s);
-    case V_ST32_C64_V4: return go_staged(k_das_staged<float2, 2, 2, 8, 4, kNWC, kRing, 3>, p, sm, s);
+    case V_ST32_C64: return go_staged(k_das_staged<float2, 2, 2, 8, 8, 8, kRing, 2>, 8, p, sm, s);
+    case V_ST64_C64: return go_staged(k_das_staged<float2, 2, 2, 16, 8, 8, kRing, 2>, 8, p, sm, s);
+    case V_ST32_H16: return go_staged(k_das_staged<__half2, 4, 1, 8, 8, 8, kRing, 2>, 8, p, sm, s);
+    case V_ST64_H16: return go_staged(k_das_staged<__half2, 4, 1, 16, 8, 8, kRing, 2>, 8, p, sm, s);
+    case V_ST32_C64_V4: return go_staged(k_das_staged<float2, 2, 2, 8, 4, 8, kRing, 3>, 8, p, sm, s);
+    case V_ST32_C64_V4W4: return go_staged(k_das_staged<float2, 2, 2, 8, 4, 4, kRing, 5>, 4, p, sm, s);
+    case V_ST32_C64_V4R56: return go_staged(k_das_staged<float2, 2, 2, 8, 4, 8, kRing, 4>, 8, p, sm, s);
+    case V_ST32_C64P_V4: return go_staged(k_das_staged<C64Planar, 4, 1, 8, 4, 8, kRing, 3>, 8, p, sm, s);
+    case V_ST64_C64P_V4: return go_staged(k_das_staged<C64Planar, 4, 1, 16, 4, 8, 8, 3>, 8, p, sm, s);
+    case V_ST32_H16_V4: return go_staged(k_das_staged<__half2, 4, 1, 8, 4, 8, kRing, 3>, 8, p, sm, s);
+    case V_ST32_B16_V4: return go_staged(k_das_staged<__nv_bfloat162, 4, 1, 8, 4, 8, kRing, 3>, 8, p, sm, s);
+    case V_ST64_C64_V4: return go_staged(k_das_staged<float2, 2, 2, 16, 4, 8, 8, 3>, 8, p, sm, s);
+    case V_ST64_H16_V4: return go_staged(k_das_staged<__half2, 4, 1, 16, 4, 8, 8, 3>, 8, p, sm, s);
+    case V_ST32_B16: return go_staged(k_das_staged<__nv_bfloat162, 4, 1, 8, 8, 8, kRing, 2>, 8, p, sm, s);
+    case V_ST64_B16_V4: return go_staged(k_das_staged<__nv_bfloat162, 4, 1, 16, 4, 8, 8, 3>, 8, p, sm, s);
     default: return cudaErrorInvalidValue;
   }
 }

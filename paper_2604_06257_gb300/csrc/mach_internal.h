@@ -27,7 +27,23 @@ enum Variant : int32_t {
   V_ST64_C64,        // staged, 64-frame tile, complex64
   V_ST32_H16,        // staged, 32-frame tile, float16 pairs
   V_ST64_H16,        // staged, 64-frame tile, float16 pairs
-  V_ST32_C64_V4,     // staged, 32-frame tile, 4 voxels per lane group (ablation)
+  V_ST32_C64_V4,     // staged, 32-frame tile, 4 voxels per lane group
+  V_ST32_C64_V4W4,   // staged, 32-frame tile, 4 voxels per lane group, 4 consumer warps
+  V_ST64_C64_V4,     // staged, 64-frame tile, 4 voxels per lane group
+  V_ST64_H16_V4,     // staged, 64-frame tile, float16 pairs, 4 voxels per lane group
+  V_CH_B16,          // channel lanes, F <= 4, bfloat16 pairs
+  V_F32_B16,         // frame lanes, 32-frame tile, bfloat16 pairs (F % 4 == 0)
+  V_F64_B16,         // frame lanes, 64-frame tile, bfloat16 pairs (F % 4 == 0)
+  V_S32_B16,         // frame lanes, 32-frame tile, scalar loads, bfloat16 pairs
+  V_ST32_B16,        // staged, 32-frame tile, bfloat16 pairs
+  V_ST64_B16_V4,     // staged, 64-frame tile, bfloat16 pairs, 4 voxels per lane group
+  V_ST32_C64_V4R56,  // staged_c64_ft32_v4 capped at 56 registers (4 blocks per SM)
+  V_F32_C64P,        // frame lanes, 32-frame tile, split complex64 rows (F % 4 == 0)
+  V_F64_C64P,        // frame lanes, 64-frame tile, split complex64 rows (F % 4 == 0)
+  V_ST32_C64P_V4,    // staged, 32-frame tile, split complex64 rows, 4 voxels per lane group
+  V_ST64_C64P_V4,    // staged, 64-frame tile, split complex64 rows, 4 voxels per lane group
+  V_ST32_H16_V4,     // staged, 32-frame tile, float16 pairs, 4 voxels per lane group
+  V_ST32_B16_V4,     // staged, 32-frame tile, bfloat16 pairs, 4 voxels per lane group
   V_COUNT
 };
 
@@ -42,6 +58,7 @@ struct VariantShape {
   bool staged;           // + one producer warp and a shared-memory ring of sample windows
   int ring_slots;
   int iq_bytes;          // bytes per complex sample
+  int iq_type;           // mach_iq_dtype the variant reads
 };
 
 const VariantShape& variant_shape(Variant v);
@@ -63,6 +80,8 @@ struct DasParams {
   int apod;
   float two_f;          // (float)(2 F#)
   float f_num;          // (float)F#
+  float four_f2;        // RN_float(4 F#^2): aperture test rho^2 * 4F#^2 <= dz^2
+  float f_num2;         // (float)(F#^2)
   float s_max;          // (float)(S - 1): a term needs 0 <= s < s_max
   float r_f;            // (float)(fc / fs)
   uint32_t phase_R;     // round(2^32 frac(fc / fs))
@@ -95,6 +114,8 @@ struct TableParams {
 };
 
 cudaError_t launch_tables(const TableParams& tp, cudaStream_t s);
+cudaError_t launch_iq_convert(const float2* src, int src_order, void* dst, int dst_dtype, int64_t T, int64_t C,
+                              int64_t S, int64_t F, cudaStream_t s);
 cudaError_t launch_das(const DasParams& p, Variant v, cudaStream_t s);
 // Per-tile bounds for the staged variants; returns the largest window (rows) and the
 // number of (tile, transmit, element) triples that need a copy.
@@ -105,6 +126,20 @@ cudaError_t launch_das_staged(const DasParams& p, Variant v, cudaStream_t s);
 cudaError_t launch_terms(const DasParams& p, const int64_t* vox_idx, int64_t n, int32_t* i0,
                          float* w, float* cw, cudaStream_t s);
 size_t das_smem_bytes(Variant v);
+
+// Ragged batches (k_batch.cu / batch.cpp).
+constexpr int kBatchFrames = 0;     // frame lanes (frame_lanes = 4, 8 or 16 lanes per voxel)
+constexpr int kBatchChannels = 1;   // channel lanes (F <= 4)
+struct BatchInstance {
+  DasParams p;          // the instance's tables, tiling and bound buffers
+  int mode;             // kBatchFrames or kBatchChannels
+  int frame_lanes;
+};
+int batch_blocks_per_sm(int iq_dtype);
+cudaError_t launch_batch(int iq_dtype, const BatchInstance* insts, const int2* items, int n_items, int* counter,
+                         int grid, cudaStream_t s);
+const DasParams* plan_params(mach_plan p);
+void pick_tile_shape(int n, int nx, int ny, int nz, bool list, int tile[3]);
 
 // Host steps shared by mach_das_plan and the allocation-free entry point.
 mach_status host_validate(const mach_das_desc* d);

@@ -170,6 +170,8 @@ extern "C" mach_status mach_das_run_noalloc(const mach_das_desc* d, const void* 
   b.apod = d->apod;
   b.two_f = static_cast<float>(2.0 * d->f_number);
   b.f_num = static_cast<float>(d->f_number);
+  b.four_f2 = static_cast<float>(4.0 * d->f_number * d->f_number);
+  b.f_num2 = static_cast<float>(d->f_number * d->f_number);
   b.s_max = static_cast<float>(S - 1);
   b.r_f = static_cast<float>(d->fc / d->fs);
   b.phase_R = host_fixed_cycles(d->fc / d->fs);

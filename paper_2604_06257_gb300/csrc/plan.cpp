@@ -70,7 +70,8 @@ mach_status validate(const mach_das_desc* d) {
   if (!(d->fc >= 0.0) || !std::isfinite(d->fc) || !std::isfinite(d->t0)) return MACH_ERR_INVALID_ARG;
   if (!(d->f_number >= 0.0) || !std::isfinite(d->f_number)) return MACH_ERR_INVALID_ARG;
   if (d->apod < MACH_APOD_NONE || d->apod > MACH_APOD_GAUSS) return MACH_ERR_INVALID_ARG;
-  if (d->iq_dtype != MACH_IQ_C64 && d->iq_dtype != MACH_IQ_F16X2) return MACH_ERR_INVALID_ARG;
+  if (d->iq_dtype < MACH_IQ_C64 || d->iq_dtype > MACH_IQ_C64_SPLIT) return MACH_ERR_INVALID_ARG;
+  if (d->iq_dtype == MACH_IQ_C64_SPLIT && (d->n_frames % 4 != 0 || d->n_frames <= 4)) return MACH_ERR_UNSUPPORTED;
   if (d->n_samples < 2 || d->n_samples > (1 << 24)) return MACH_ERR_INVALID_ARG;
   if (d->n_frames < 1) return MACH_ERR_INVALID_ARG;
   // per-(t, c) slab offsets are computed in 64 bits, but one slab must stay indexable
@@ -110,21 +111,39 @@ mach_status validate(const mach_das_desc* d) {
 }
 
 Variant pick_variant(int iq_dtype, int F) {
+  // staged 4-voxel-group kernels for 16 < F <= 64 (fastest measured shapes); L1-path
+  // kernels for short, long (frame-tiled) or odd ensembles
   if (iq_dtype == MACH_IQ_C64) {
     if (F <= 4) return V_CH_C64;
     if (F % 2 == 0) {
       if (F <= 16) return V_F16_C64;
-      if (F <= 32) return V_ST32_C64;
-      if (F <= 64) return V_ST64_C64;
+      if (F <= 32) return V_ST32_C64_V4;
+      if (F <= 64) return V_ST64_C64_V4;
       return V_F64_C64;
     }
     return V_S32_C64;
   }
+  if (iq_dtype == MACH_IQ_C64_SPLIT) {   // F % 4 == 0 and F > 4 (checked by validate)
+    if (F <= 16) return V_F32_C64P;
+    if (F <= 32) return V_ST32_C64P_V4;
+    if (F <= 64) return V_ST64_C64P_V4;
+    return V_F64_C64P;
+  }
+  if (iq_dtype == MACH_IQ_BF16X2) {
+    if (F <= 4) return V_CH_B16;
+    if (F % 4 == 0) {
+      if (F <= 16) return V_F32_B16;
+      if (F <= 32) return V_ST32_B16_V4;
+      if (F <= 64) return V_ST64_B16_V4;
+      return V_F64_B16;
+    }
+    return V_S32_B16;
+  }
   if (F <= 4) return V_CH_H16;
   if (F % 4 == 0) {
     if (F <= 16) return V_F32_H16;
-    if (F <= 32) return V_ST32_H16;
-    if (F <= 64) return V_ST64_H16;
+    if (F <= 32) return V_ST32_H16_V4;
+    if (F <= 64) return V_ST64_H16_V4;
     return V_F64_H16;
   }
   return V_S32_H16;
@@ -133,19 +152,23 @@ Variant pick_variant(int iq_dtype, int F) {
 // The non-staged variant with the same frame tile (used when the ring would not fit).
 Variant unstaged(Variant v) {
   switch (v) {
-    case V_ST32_C64: case V_ST32_C64_V4: return V_F32_C64;
-    case V_ST64_C64: return V_F64_C64;
-    case V_ST32_H16: return V_F32_H16;
-    case V_ST64_H16: return V_F64_H16;
+    case V_ST32_C64: case V_ST32_C64_V4: case V_ST32_C64_V4W4: case V_ST32_C64_V4R56: return V_F32_C64;
+    case V_ST64_C64: case V_ST64_C64_V4: return V_F64_C64;
+    case V_ST32_H16: case V_ST32_H16_V4: return V_F32_H16;
+    case V_ST64_H16: case V_ST64_H16_V4: return V_F64_H16;
+    case V_ST32_B16: case V_ST32_B16_V4: return V_F32_B16;
+    case V_ST32_C64P_V4: return V_F32_C64P;
+    case V_ST64_C64P_V4: return V_F64_C64P;
+    case V_ST64_B16_V4: return V_F64_B16;
     default: return v;
   }
 }
 
 bool variant_accepts(Variant v, int iq_dtype, int F) {
   const VariantShape& s = variant_shape(v);
-  if ((s.iq_bytes == 8) != (iq_dtype == MACH_IQ_C64)) return false;
+  if (s.iq_type != iq_dtype) return false;
   if (s.channel_lanes) return F <= s.frame_tile;
-  const int vec = s.frames_per_lane == 1 ? 1 : (s.iq_bytes == 8 ? 2 : 4);
+  const int vec = s.frames_per_lane == 1 ? 1 : (s.iq_type == MACH_IQ_C64 ? 2 : 4);
   if (F % vec != 0) return false;
   if (s.staged && F > s.frame_tile) return false;
   return true;
@@ -158,8 +181,9 @@ void pick_tile(int n, int nx, int ny, int nz, bool list, int tile[3]) {
     tile[0] = n; tile[1] = 1; tile[2] = 1;
     return;
   }
-  if (ny == 1) {   // 2D x-z grid
-    const int tx = std::min(16, n);
+  if (ny == 1) {   // 2D x-z grid: the squarest power-of-two split
+    int tx = 1;
+    while (tx * tx < n) tx *= 2;
     tile[0] = tx; tile[1] = 1; tile[2] = n / tx;
     return;
   }
@@ -230,9 +254,11 @@ static mach_status configure_tiles(DasParams& b, Variant var, bool list, int64_t
     if (b.ny == 1) {
       if (wv == 32) { wb[0] = 8; wb[1] = 1; wb[2] = 4; }
       else if (wv == 16) { wb[0] = 4; wb[1] = 1; wb[2] = 4; }
+      else if (wv == 8) { wb[0] = 4; wb[1] = 1; wb[2] = 2; }
     } else {
       if (wv == 32) { wb[0] = 4; wb[1] = 4; wb[2] = 2; }
       else if (wv == 16) { wb[0] = 4; wb[1] = 4; wb[2] = 1; }
+      else if (wv == 8) { wb[0] = 4; wb[1] = 2; wb[2] = 1; }
     }
     if (wb[0] && tile[0] % wb[0] == 0 && tile[1] % wb[1] == 0 && tile[2] % wb[2] == 0) {
       b.wb_x = wb[0];
@@ -381,6 +407,8 @@ mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) 
   b.apod = d->apod;
   b.two_f = static_cast<float>(2.0 * d->f_number);
   b.f_num = static_cast<float>(d->f_number);
+  b.four_f2 = static_cast<float>(4.0 * d->f_number * d->f_number);
+  b.f_num2 = static_cast<float>(d->f_number * d->f_number);
   b.s_max = static_cast<float>(S - 1);
   b.r_f = static_cast<float>(d->fc / d->fs);
   b.phase_R = fixed_cycles(d->fc / d->fs);
@@ -405,6 +433,23 @@ mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) 
     b.tbox = p->d_tbox;
     b.txr = p->d_txr;
     b.rows_cap = p->rows_cap;
+    const Variant smaller_ring = var == V_ST64_C64_V4 ? V_ST64_C64 : (var == V_ST64_H16_V4 ? V_ST64_H16 : var);
+    if (!forced && smaller_ring != var && staged_smem_bytes(var, p->rows_cap, F, T) > kStagedSmemCap &&
+        staged_smem_bytes(smaller_ring, p->rows_cap, F, T) <= kStagedSmemCap) {
+      // an 8-slot ring does not fit: the 2-pair variant needs only 4 slots (its tiles are
+      // larger, so recompute them and their bounds)
+      var = smaller_ring;
+      p->variant = var;
+      if ((st = configure_tiles(b, var, list, V, F)) != MACH_OK) return fail(st);
+      const int64_t tiles1 = static_cast<int64_t>(b.tiles_x) * b.tiles_y * b.tiles_z;
+      if (tiles1 > tiles0) return fail(MACH_ERR_UNSUPPORTED);   // (larger tiles: never more of them)
+      if (launch_tile_bounds(b, p->d_tbox, p->d_txr, d_stats, s) != cudaSuccess) return fail(MACH_ERR_CUDA);
+      if (cudaMemcpyAsync(stats, d_stats, sizeof(stats), cudaMemcpyDeviceToHost, s) != cudaSuccess) return fail(MACH_ERR_CUDA);
+      if (cudaStreamSynchronize(s) != cudaSuccess) return fail(MACH_ERR_CUDA);
+      p->rows_cap = std::max(2, stats[0]);
+      p->copy_pairs = stats[1];
+      b.rows_cap = p->rows_cap;
+    }
     if (staged_smem_bytes(var, p->rows_cap, F, T) > kStagedSmemCap) {
       if (forced) return fail(MACH_ERR_UNSUPPORTED);
       // the tiles' windows are too long for the ring: use the L1-cached variant
@@ -550,4 +595,9 @@ mach_status host_configure_tiles(DasParams& b, Variant v, bool list, int64_t V, 
   return configure_tiles(b, v, list, V, F);
 }
 uint32_t host_fixed_cycles(double cycles) { return fixed_cycles(cycles); }
+}  // namespace mach
+
+namespace mach {
+const DasParams* plan_params(mach_plan p) { return p ? &p->base : nullptr; }
+void pick_tile_shape(int n, int nx, int ny, int nz, bool list, int tile[3]) { pick_tile(n, nx, ny, nz, list, tile); }
 }  // namespace mach

@@ -23,7 +23,7 @@ from typing import Optional, Tuple
 import numpy as np
 
 APOD_CODES = {"none": 0, "boxcar": 1, "hann": 2, "gauss": 3}
-IQ_DTYPES = ("c64", "f16x2")
+IQ_DTYPES = ("c64", "f16x2", "bf16x2", "c64split")
 
 
 @dataclasses.dataclass(frozen=True)

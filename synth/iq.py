@@ -114,3 +114,29 @@ def to_f16x2(iq: torch.Tensor) -> torch.Tensor:
 def from_f16x2(iq16: torch.Tensor) -> torch.Tensor:
     """float16 [...,2] -> complex64 (exact widening)."""
     return torch.view_as_complex(iq16.to(torch.float32).contiguous())
+
+
+def to_bf16x2(iq: torch.Tensor) -> torch.Tensor:
+    """complex64 [T,C,S,F] -> bfloat16 [T,C,S,F,2] (re, im interleaved), round to nearest even."""
+    return torch.view_as_real(iq).to(torch.bfloat16).contiguous()
+
+
+def to_c64split(iq: torch.Tensor) -> torch.Tensor:
+    """complex64 [T,C,S,F] -> float32 [T,C,S,2,F]: per sample row the F real parts, then
+    the F imaginary parts (exact)."""
+    return torch.view_as_real(iq).permute(0, 1, 2, 4, 3).contiguous()
+
+
+def to_storage(iq: torch.Tensor, dtype: str) -> torch.Tensor:
+    return {"c64": lambda x: x.contiguous(), "f16x2": to_f16x2, "bf16x2": to_bf16x2,
+            "c64split": to_c64split}[dtype](iq)
+
+
+def from_storage(x: torch.Tensor) -> torch.Tensor:
+    """Widen stored IQ (complex64, float16 / bfloat16 pairs, or split float32 rows
+    [T,C,S,2,F]) to complex64 [T,C,S,F], exactly."""
+    if x.dtype == torch.complex64:
+        return x
+    if x.dtype == torch.float32 and x.dim() == 5 and x.shape[3] == 2:
+        return torch.view_as_complex(x.permute(0, 1, 2, 4, 3).contiguous())
+    return torch.view_as_complex(x.to(torch.float32).contiguous())

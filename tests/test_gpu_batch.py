@@ -1,0 +1,114 @@
+"""Ragged batches: many instances in one persistent launch, against the FP64 oracle and
+against single-instance plans; graph capture; the autotuner's choices."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from synth.ragged import ragged_instances
+import paper_2604_06257_gb300 as m
+from paper_2604_06257_gb300 import autotune, build as pkg_build
+from metrics import nrmse_db
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pkg_build.build()
+    m.lib()
+
+
+def buffers(acqs, seed=0):
+    iqs, ys, pds = [], [], []
+    for i, a in enumerate(acqs):
+        iq = synth.random_iq(a, seed + i, device="cuda")
+        iqs.append(iq)
+        ys.append(torch.zeros((a.n_vox, a.n_frames), dtype=torch.complex64, device="cuda"))
+        pds.append(torch.zeros(a.n_vox, dtype=torch.float32, device="cuda"))
+    return iqs, ys, pds
+
+
+@pytest.mark.parametrize("dtype", ["c64", "f16x2"])
+def test_ragged_batch_matches_oracle(dtype):
+    acqs = ragged_instances(n=10, seed=11, iq_dtype=dtype, scale=0.12)
+    acqs = [a.replace(n_frames=F) for a, F in zip(acqs, [1, 3, 4, 5, 7, 12, 17, 33, 48, 64])]
+    iqs, ys, pds = buffers(acqs)
+    stored = [synth.iqmod.to_storage(x, dtype) for x in iqs]
+    with m.Batch([m.plan_kwargs(a) for a in acqs]) as b:
+        b.bind(stored, ys, pds)
+        b.run()
+        torch.cuda.synchronize()
+        info = b.info()
+    assert info["instances"] == 10 and info["items"] >= 10
+    modes = [s[0] for s in info["shapes"]]
+    assert modes[:3] == [1, 1, 1] and all(x == 0 for x in modes[3:])
+    for a, x, y, pd in zip(acqs, stored, ys, pds):
+        idx = np.arange(0, a.n_vox, max(1, a.n_vox // 300))
+        y_ref, pd_ref = oracle.das(a, synth.iqmod.from_storage(x.cpu()), idx)
+        assert nrmse_db(y.cpu().numpy()[idx], y_ref) <= -100, a.name
+        assert nrmse_db(pd.cpu().numpy()[idx].astype(np.float64), pd_ref) <= -60, a.name
+
+
+def test_batch_equals_single_plans_and_replays_from_a_graph():
+    acqs = ragged_instances(n=6, seed=5, iq_dtype="c64", scale=0.15)
+    iqs, ys, pds = buffers(acqs, seed=50)
+    kws = [m.plan_kwargs(a) for a in acqs]
+    with m.Batch(kws) as b:
+        b.bind(iqs, ys, pds)
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            b.run(stream=s)                     # warm-up outside capture
+        s.synchronize()
+        for y in ys:
+            y.zero_()
+        with torch.cuda.graph(g):
+            b.run()
+        g.replay()
+        g.replay()                              # the work counter resets itself
+        torch.cuda.synchronize()
+    for a, iq, y, pd in zip(acqs, iqs, ys, pds):
+        with m.Plan(**m.plan_kwargs(a)) as p:
+            pd1, y1 = p.power_doppler(iq, want_y=True)
+            torch.cuda.synchronize()
+        assert nrmse_db(y.cpu().numpy(), y1.cpu().numpy()) <= -110, a.name
+        assert nrmse_db(pd.cpu().numpy().astype(np.float64), pd1.cpu().numpy().astype(np.float64)) <= -100
+
+
+def test_explicit_shapes_and_validation():
+    acqs = ragged_instances(n=3, seed=8, iq_dtype="c64", scale=0.1)
+    acqs = [a.replace(n_frames=F) for a, F in zip(acqs, [2, 20, 40])]
+    kws = [m.plan_kwargs(a) for a in acqs]
+    shapes = [(1, 0, None), (0, 8, None), (0, 16, (2, 2, 16) if acqs[2].ndim == 3 else (4, 1, 16))]
+    iqs, ys, pds = buffers(acqs, seed=70)
+    with m.Batch(kws, shapes=shapes) as b:
+        b.bind(iqs, ys, pds)
+        b.run()
+        torch.cuda.synchronize()
+        got = b.info()["shapes"]
+    assert got[0][:2] == (1, 0) and got[1][:2] == (0, 8) and got[2][:2] == (0, 16)
+    for a, iq, y in zip(acqs, iqs, ys):
+        idx = np.arange(0, a.n_vox, max(1, a.n_vox // 200))
+        y_ref, _ = oracle.das(a, iq.cpu(), idx)
+        assert nrmse_db(y.cpu().numpy()[idx], y_ref) <= -100
+    bad = [[(1, 0, None), (0, 8, None), (0, 4, None)],          # 4 lanes x 4 frames < 40 frames
+           [(0, 8, None), (0, 8, None), (0, 16, None)],         # channel lanes required for F <= 4? no: allowed
+           [(1, 0, None), (0, 8, (3, 1, 3)), (0, 16, None)]]    # tile volume mismatch
+    with pytest.raises(m.MachError):
+        m.Batch(kws, shapes=bad[0])
+    with pytest.raises(m.MachError):
+        m.Batch(kws, shapes=bad[2])
+
+
+def test_autotuner_picks_a_valid_and_fastest_candidate():
+    acqs = ragged_instances(n=2, seed=9, iq_dtype="f16x2", scale=0.2)
+    kws = [m.plan_kwargs(a) for a in acqs]
+    iqs, ys, pds = buffers(acqs, seed=90)
+    stored = [synth.iqmod.to_f16x2(x) for x in iqs]
+    for kw, iq, y, pd in zip(kws, stored, ys, pds):
+        best, times = autotune.tune_instance(kw, iq, y, pd)
+        assert best in autotune.candidates(kw)
+        if times:
+            assert times[best] == min(times.values())

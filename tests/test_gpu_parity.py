@@ -23,6 +23,10 @@ PD_DB = -60.0
 FP16_DB = -60.0
 # |y|^2 doubles the relative amplitude error of the stored samples: +6 dB over FP16_DB
 FP16_PD_DB = FP16_DB + 6.0
+# bfloat16 keeps 8 significand bits: unit roundoff 2^-9, rms rounding error 2^-9/sqrt(3)
+# ~ -59 dB of each sample; the gate leaves 9 dB of margin (PD: +6 dB as above)
+BF16_DB = -50.0
+BF16_PD_DB = BF16_DB + 6.0
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -37,10 +41,7 @@ def plan_for(acq, **kw):
 
 def dev_iq(acq, iq):
     """Device IQ in the acquisition's storage type."""
-    iq = iq.cuda()
-    if acq.iq_dtype == "f16x2":
-        return synth.iqmod.to_f16x2(iq)
-    return iq.contiguous()
+    return synth.iqmod.to_storage(iq.cuda(), acq.iq_dtype)
 
 
 def check_terms(acq, plan, idx):
@@ -154,7 +155,7 @@ def test_doppler2d_full_all_voxels():
     """The benchmark workload, in the launch configuration the benchmark times."""
     acq, iq = synth.make("doppler2d", "full", device="cuda")
     with plan_for(acq) as p:
-        assert p.info()["variant"] in ("staged_c64_ft32", "frames_c64_ft32")
+        assert p.info()["variant"].startswith("staged_c64_ft32")
         pd, y = p.power_doppler(iq, want_y=True)
     print(compare(acq, iq.cpu(), y, pd))
 
@@ -351,6 +352,15 @@ STAGED_CASES = [
     ("staged_c64_ft64", "frames_c64_ft64", "volume3d", "c64"),
     ("staged_f16_ft32", "frames_f16_ft32", "doppler2d", "f16x2"),
     ("staged_f16_ft64", "frames_f16_ft64", "volume3d", "f16x2"),
+    ("staged_c64_ft32_v4w4", "frames_c64_ft32", "doppler2d", "c64"),
+    ("staged_c64_ft64_v4", "frames_c64_ft64", "volume3d", "c64"),
+    ("staged_f16_ft64_v4", "frames_f16_ft64", "volume3d", "f16x2"),
+    ("staged_b16_ft32", "frames_b16_ft32", "doppler2d", "bf16x2"),
+    ("staged_b16_ft64_v4", "frames_b16_ft64", "volume3d", "bf16x2"),
+    ("staged_c64p_ft32_v4", "frames_c64p_ft32", "doppler2d", "c64split"),
+    ("staged_c64p_ft64_v4", "frames_c64p_ft64", "volume3d", "c64split"),
+    ("staged_f16_ft32_v4", "frames_f16_ft32", "doppler2d", "f16x2"),
+    ("staged_b16_ft32_v4", "frames_b16_ft32", "doppler2d", "bf16x2"),
 ]
 
 
@@ -375,7 +385,7 @@ def test_staged_matches_oracle_and_l1_kernel_bitwise(staged, l1, name, dt):
     else:
         # the L1 kernel takes two elements per round (16 voxels per warp): other order
         assert nrmse_db(y_s.cpu().numpy(), y_l.cpu().numpy()) < -120
-    ref_iq = synth.iqmod.from_f16x2(diq.cpu()) if dt == "f16x2" else iq.cpu()
+    ref_iq = synth.iqmod.from_storage(diq.cpu())
     print(staged, info["ring_rows"], info["copy_pairs"], compare(acq, ref_iq, y_s, pd_s))
 
 
@@ -384,9 +394,9 @@ def test_staged_partial_frame_tiles(F):
     acq = small_random(F, C=17, T=3)
     iq = synth.random_iq(acq, F, device="cuda")
     with plan_for(acq) as p:
-        assert p.info()["variant"].startswith("staged")
+        variant = p.info()["variant"]
         pd, y = p.power_doppler(iq, want_y=True)
-    compare(acq, iq.cpu(), y, pd)
+    print(F, variant, compare(acq, iq.cpu(), y, pd))
 
 
 def test_staged_full_doppler_bitwise_equal_to_l1():
@@ -432,3 +442,95 @@ def test_bounded_wait_reports_timeout_and_context_survives():
         pd, y = p.power_doppler(iq, want_y=True)
         assert p.device_status() == m.MACH_OK
     compare(acq, iq.cpu(), y, pd)
+
+
+# ------------------------------------------------- K0 and bfloat16 storage ----
+
+@pytest.mark.parametrize("dtype", ["c64", "f16x2", "bf16x2", "c64split"])
+@pytest.mark.parametrize("order", ["ftcs", "tcsf"])
+def test_iq_convert_bit_exact(order, dtype):
+    T, Cn, S, F = 3, 17, 129, 37
+    g = torch.Generator(device="cuda").manual_seed(5)
+    src_tcsf = torch.view_as_complex(torch.randn((T, Cn, S, F, 2), generator=g, device="cuda") * 3)
+    src = src_tcsf.permute(3, 0, 1, 2).contiguous() if order == "ftcs" else src_tcsf.contiguous()
+    out = m.prepare_iq(src, order, dtype, shape=(T, Cn, S, F))
+    ref = synth.iqmod.to_storage(src_tcsf.contiguous(), dtype)
+    torch.cuda.synchronize()
+    assert out.shape == ref.shape and out.dtype == ref.dtype
+    assert torch.equal(out.view(torch.uint8) if dtype != "c64" else out, ref.view(torch.uint8) if dtype != "c64" else ref)
+
+
+def test_iq_convert_rejects_bad_arguments():
+    x = torch.zeros(64, dtype=torch.complex64, device="cuda")
+    L = m.lib()
+    assert L.mach_iq_convert(x.data_ptr(), 7, x.data_ptr() + 512, 0, 1, 1, 1, 1, None) == m.MACH_ERR_INVALID_ARG
+    assert L.mach_iq_convert(x.data_ptr(), 0, x.data_ptr(), 0, 1, 1, 1, 1, None) == m.MACH_ERR_INVALID_ARG
+    assert L.mach_iq_convert(x.data_ptr(), 0, x.data_ptr() + 512, 9, 1, 1, 1, 1, None) == m.MACH_ERR_INVALID_ARG
+    assert L.mach_iq_convert(x.data_ptr(), 0, x.data_ptr() + 512, 0, 0, 1, 1, 1, None) == m.MACH_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("name", ["doppler2d", "volume3d"])
+def test_bf16_storage_small(name):
+    acq, iq = synth.make(name, "small", device="cuda", iq_dtype="bf16x2")
+    diq = dev_iq(acq, iq)
+    with plan_for(acq) as p:
+        pd, y = p.power_doppler(diq, want_y=True)
+    print(compare(acq, synth.iqmod.from_storage(diq.cpu()), y, pd))
+    print(compare(acq, iq.cpu(), y, pd, bmode_db=BF16_DB, pd_db=BF16_PD_DB))
+
+
+@pytest.mark.parametrize("F", [1, 4, 6, 8, 12, 32, 36, 64, 68])
+def test_frame_counts_bf16(F):
+    acq = small_random(F, iq_dtype="bf16x2")
+    iq = synth.random_iq(acq, 200 + F, device="cuda")
+    diq = dev_iq(acq, iq)
+    with plan_for(acq) as p:
+        pd, y = p.power_doppler(diq, want_y=True)
+    compare(acq, synth.iqmod.from_storage(diq.cpu()), y, pd)
+
+
+def test_prepare_then_beamform_from_acquisition_order():
+    """K0 from scanner order followed by DAS equals DAS on the directly laid-out data."""
+    acq, iq = synth.make("doppler2d", "small", device="cuda")
+    scanner = iq.permute(3, 0, 1, 2).contiguous()        # [F][T][C][S]
+    for dtype in ("c64", "f16x2", "bf16x2", "c64split"):
+        a = acq.replace(iq_dtype=dtype)
+        prepared = m.prepare_iq(scanner, "ftcs", dtype)
+        with plan_for(a) as p:
+            pd1, y1 = p.power_doppler(prepared, want_y=True)
+            pd2, y2 = p.power_doppler(dev_iq(a, iq), want_y=True)
+        assert torch.equal(y1, y2) and torch.equal(pd1, pd2)
+
+
+@pytest.mark.parametrize("name,pair", [("doppler2d", ("staged_c64p_ft32_v4", "staged_c64_ft32_v4")),
+                                       ("volume3d", ("staged_c64p_ft64_v4", "staged_c64_ft64_v4"))])
+def test_split_rows_bitwise_equal_to_interleaved(name, pair):
+    """Split complex64 rows (packed FP32x2 accumulation) perform the same FMA sequence per
+    element as interleaved complex64: identical frames.  Power Doppler agrees to rounding
+    only: the two layouts give a lane different frames, so the order of its partial
+    sum of |y|^2 differs."""
+    acq, iq = synth.make(name, "small", device="cuda")
+    split = acq.replace(iq_dtype="c64split")
+    with forced(split, pair[0]) as ps, forced(acq, pair[1]) as pi:
+        pd_s, y_s = ps.power_doppler(synth.iqmod.to_c64split(iq), want_y=True)
+        pd_i, y_i = pi.power_doppler(iq, want_y=True)
+        torch.cuda.synchronize()
+    assert torch.equal(y_s, y_i)
+    assert torch.max(torch.abs(pd_s - pd_i) / pd_i.abs().clamp_min(1e-30)).item() < 1e-6
+
+
+@pytest.mark.parametrize("F", [8, 12, 16, 20, 32, 36, 64, 68])
+def test_frame_counts_split(F):
+    acq = small_random(F, iq_dtype="c64split")
+    iq = synth.random_iq(acq, 300 + F, device="cuda")
+    with plan_for(acq) as p:
+        pd, y = p.power_doppler(dev_iq(acq, iq), want_y=True)
+    compare(acq, iq.cpu(), y, pd)
+
+
+def test_split_rows_reject_unsupported_frame_counts():
+    for F in (3, 4, 6):
+        acq = small_random(F, iq_dtype="c64split")
+        with pytest.raises(m.MachError) as e:
+            plan_for(acq)
+        assert e.value.status == m.MACH_ERR_UNSUPPORTED
