@@ -47,7 +47,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", default="", help="force a kernel variant (ablations)")
-    ap.add_argument("--iq-dtype", default="c64", choices=["c64", "f16x2", "bf16x2", "c64split"])
+    ap.add_argument("--ragged-n", type=int, default=64, help="instances of the ragged batch")
+    ap.add_argument("--ragged-scale", type=float, default=1.0, help="grid scale of the ragged batch")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--iq-dtype", default="c64split", choices=["c64", "f16x2", "bf16x2", "c64split"],
+                    help="IQ storage the timed kernel reads (prepared by K0 outside the timed region)")
     return ap.parse_args()
 
 
@@ -144,6 +148,7 @@ class Clocks:
 
 
 DESCRIBE = {"doppler2d": "rotating-disk Doppler stand-in (Sec. 4.1 shape)",
+            "ulm3d": "3D ULM shape (Sec. 6: 94x94x178 voxels, 1024 el, 5 angles)",
             "volume3d": "32x32 matrix-array volume (Sec. 6 shape)",
             "bmode2d": "steered plane-wave B-mode (Sec. 2.1 compounding)"}
 
@@ -231,8 +236,11 @@ def run_ours(args):
 
     acq, iq = synth.make(args.workload, "full", device=dev, seed=synth.SEEDS[args.workload] + rank,
                          iq_dtype=args.iq_dtype)
+    iq_c64 = iq                                     # complex64 [T, C, S, F]
     if args.iq_dtype != "c64":
-        iq = synth.iqmod.to_storage(iq, args.iq_dtype)
+        # K0 from the acquisition order [F, T, C, S] into the kernels' layout (untimed
+        # preparation, as the paper excludes format conversion from its timing)
+        iq = m.prepare_iq(iq_c64.permute(3, 0, 1, 2).contiguous(), "ftcs", args.iq_dtype)
     if args.variant:
         m.mach_debug_force_variant(args.variant)
     plan = m.Plan(**m.plan_kwargs(acq))
@@ -307,9 +315,9 @@ def run_ours(args):
     # K0 (channel-data preparation): acquisition order -> frame-contiguous layout, per
     # storage type; HBM-bound, so it is reported against the measured copy bandwidth
     k0 = {}
-    if args.iq_dtype == "c64":
+    if True:
         T_, C_, S_, F_ = acq.iq_shape
-        scanner = iq.permute(3, 0, 1, 2).contiguous()
+        scanner = iq_c64.permute(3, 0, 1, 2).contiguous()
         n = scanner.numel()
         for dt, ob in (("c64", 8), ("c64split", 8), ("f16x2", 4), ("bf16x2", 4)):
             out = m.prepare_iq(scanner, "ftcs", dt)
@@ -330,18 +338,41 @@ def run_ours(args):
                       "frac": byts / t / 1e9 / hbm_peak}
         del scanner, out
 
-    # end to end through the public API with host buffers (pinned), copies timed
+    # the same step on interleaved complex64 rows, for comparison with the split layout
+    alt = {}
+    if args.iq_dtype == "c64split" and not args.variant:
+        acq_i = acq.replace(iq_dtype="c64")
+        with m.Plan(**m.plan_kwargs(acq_i)) as pi:
+            for _ in range(args.warmup):
+                flush.zero_()
+                m.mach_power_doppler(pi.handle, iq_c64, pd, y)
+            ts = []
+            for _ in range(min(args.steps, 1000)):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                m.mach_power_doppler(pi.handle, iq_c64, pd, y)
+                e1.record(stream)
+                ts.append((e0, e1))
+            torch.cuda.synchronize()
+            tt = statistics.mean(a.elapsed_time(b) for a, b in ts) / 1e3
+            alt["c64_interleaved"] = {"value": acq.points / tt, "ms_per_step": tt * 1e3,
+                                      "variant": pi.info()["variant"]}
+
+    # end to end through the public API with host buffers (pinned), copies timed: the host
+    # holds complex64 IQ in acquisition order; each step copies it in, converts it (K0),
+    # beamforms and copies the frames and Power Doppler out
     e2e = None
     if args.e2e_steps > 0:
-        iq_pin = iq.cpu().pin_memory()
+        iq_pin = iq_c64.permute(3, 0, 1, 2).contiguous().cpu().pin_memory()
         pd_pin = torch.empty(V, dtype=torch.float32).pin_memory()
         y_pin = torch.empty((V, F), dtype=torch.complex64).pin_memory()
         for _ in range(3):
-            plan.power_doppler_host(iq_pin, pd_pin, y_pin)
+            plan.power_doppler_host(iq_pin, pd_pin, y_pin, order="ftcs")
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            plan.power_doppler_host(iq_pin, pd_pin, y_pin)
+            plan.power_doppler_host(iq_pin, pd_pin, y_pin, order="ftcs")
         te = shard.max_over_ranks(time.perf_counter() - t0)
         e2e = {"value": world * acq.points * args.e2e_steps / te, "unit": UNIT,
                "h2d_bytes_per_step": iq_pin.numel() * iq_pin.element_size(),
@@ -350,17 +381,23 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(acq, iq.cpu(), args.cpu_seconds)
+        cpu = oracle_sample(acq, iq_c64.cpu(), args.cpu_seconds)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if args.iq_dtype == "c64" else f"f32 ({args.iq_dtype} IQ storage)", "data": "synthetic",
+                "dtype": "f32" if args.iq_dtype in ("c64", "c64split") else f"f32 ({args.iq_dtype} IQ storage)",
+                "data": "synthetic",
                 "config": workload_config(acq, {"parallelism": f"replicas{world}",
+                                                "iq_layout": {"c64split": "complex64 values, each sample row split "
+                                                              "into F real then F imaginary parts (K0 output)",
+                                                              "c64": "interleaved complex64"}.get(args.iq_dtype,
+                                                                                                  args.iq_dtype),
                                                 "kernel_variant": info["variant"],
                                                 "active_fraction": active_terms / (V * acq.n_elem * acq.n_tx)}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "plan": info, "k0_iq_convert": k0,
+                "other_layouts": alt,
                 "gpu_launches": launches_per_step * args.steps,
                 "clocks": clk, "wall_s_timed_region": t_wall,
                 "paper_context": {"points_per_s": PAPER_POINTS_PER_S,
@@ -369,6 +406,81 @@ def run_ours(args):
                                   "ratio": value / PAPER_POINTS_PER_S}}
         print(json.dumps(line))
     plan.close()
+
+
+# ------------------------------------------------------------- ragged batch ----
+
+def run_ragged(args):
+    """64 seeded instances (2D and 3D, 1-48 frames, 1-15 transmits, float16 IQ) in one
+    persistent launch: default shapes, autotuned shapes, and the same instances beamformed
+    one plan after another."""
+    import torch
+    import synth
+    from synth.ragged import ragged_instances
+    import paper_2604_06257_gb300 as m
+    from paper_2604_06257_gb300 import autotune, build as pkg_build
+
+    pkg_build.build()
+    m.lib()
+    acqs = ragged_instances(n=args.ragged_n, seed=4, iq_dtype="f16x2", scale=args.ragged_scale)
+    kws = [m.plan_kwargs(a) for a in acqs]
+    iqs, ys, pds = [], [], []
+    for i, a in enumerate(acqs):
+        iqs.append(synth.iqmod.to_f16x2(synth.random_iq(a, 1000 + i, device="cuda")))
+        ys.append(torch.empty((a.n_vox, a.n_frames), dtype=torch.complex64, device="cuda"))
+        pds.append(torch.empty(a.n_vox, dtype=torch.float32, device="cuda"))
+    points = sum(a.points for a in acqs)
+
+    def timed(fn, steps):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / steps
+
+    steps = max(1, min(args.steps, 10))
+    out = {}
+    with m.Batch(kws) as b:
+        b.bind(iqs, ys, pds)
+        t_def = timed(b.run, steps)
+        out["batch_default"] = {"s": t_def, "value": points / t_def, "info": {k: v for k, v in b.info().items()
+                                                                              if k != "shapes"}}
+    t0 = time.perf_counter()
+    shapes = None if args.no_autotune else autotune.tune_batch(kws, iqs, ys, pds)
+    t_tune = time.perf_counter() - t0
+    with m.Batch(kws, shapes=shapes) as b:
+        b.bind(iqs, ys, pds)
+        t_tuned = timed(b.run, steps)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            b.run()
+        t_graph = timed(g.replay, steps)
+    plans = [m.Plan(**kw) for kw in kws]
+
+    def seq():
+        for pl, iq, y, pd in zip(plans, iqs, ys, pds):
+            m.mach_power_doppler(pl.handle, iq, pd, y)
+    t_seq = timed(seq, steps)
+    for pl in plans:
+        pl.close()
+    line = {"metric": "ragged batch DAS points/s (Eq. 1 summed over 64 instances)", "value": points / t_graph,
+            "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": t_graph * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f16x2 IQ storage)",
+            "data": "synthetic",
+            "config": {"workload": f"{len(acqs)} seeded instances: 2D 64-256 el / 128^2-384^2 px and 3D "
+                                   f"256-1024 el / 64^3-112^3 voxels (grid scale {args.ragged_scale}), 1-48 "
+                                   "frames, 1-15 transmits, log-uniform sizes (seed 4)",
+                       "points_per_step": points, "autotune_s": t_tune, "autotuned": shapes is not None},
+            "batch_graph_autotuned": {"s": t_graph, "value": points / t_graph},
+            "batch_autotuned": {"s": t_tuned, "value": points / t_tuned},
+            **out,
+            "sequential_plans": {"s": t_seq, "value": points / t_seq}}
+    print(json.dumps(line))
 
 
 # ---------------------------------------------------------- reference arm ----
@@ -427,6 +539,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "ragged":
+        run_ragged(args)
     else:
         run_ours(args)
     try:

@@ -431,16 +431,28 @@ class Plan:
             return pd.cpu(), (y.cpu() if y is not None else None)
         return pd, y
 
-    def power_doppler_host(self, iq_host, pd_host, y_host=None, stream=None):
+    def power_doppler_host(self, iq_host, pd_host, y_host=None, stream=None, order=None):
         """Host buffers in and out (pinned memory recommended): copies the IQ to the
         device, beamforms, copies Power Doppler (and the frames, if ``y_host`` is given)
-        back, and returns once the results are in host memory."""
+        back, and returns once the results are in host memory.  With ``order`` ("ftcs":
+        complex64 [F, T, C, S] acquisition order, or "tcsf": complex64 [T, C, S, F]) the
+        host data are complex64 and K0 converts them on the device to the plan's layout."""
         torch = self._torch
-        self._check_iq(iq_host)
         s = torch.cuda.current_stream() if stream is None else stream
         with torch.cuda.stream(s):
-            dev = self._buf("iq", tuple(iq_host.shape), iq_host.dtype)
-            dev.copy_(iq_host, non_blocking=True)
+            raw = self._buf("raw", tuple(iq_host.shape), iq_host.dtype)
+            raw.copy_(iq_host, non_blocking=True)
+            if order is None:
+                self._check_iq(iq_host)
+                dev = raw
+            else:
+                T, Cn, S, F = self.iq_shape
+                shape = (T, Cn, S, 2, F) if self.iq_dtype == "c64split" else (
+                    (T, Cn, S, F) if self.iq_dtype == "c64" else (T, Cn, S, F, 2))
+                dt = {"c64": torch.complex64, "c64split": torch.float32, "f16x2": torch.float16,
+                      "bf16x2": torch.bfloat16}[self.iq_dtype]
+                dev = self._buf("iq", shape, dt)
+                mach_iq_convert(raw, order, dev, self.iq_dtype, T, Cn, S, F, s)
             pd_d = self._buf("pd", (self.n_vox,), torch.float32)
             y_d = (self._buf("y", (self.n_vox, self.n_frames), torch.complex64)
                    if y_host is not None else None)

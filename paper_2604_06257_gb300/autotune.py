@@ -2,6 +2,8 @@
 
 For one instance, every candidate (lane mapping, tile box) is timed on a one-instance
 batch with CUDA events (median of a few launches after a warm-up) and the fastest kept.
+Large instances are timed on a slab of their grid (the first ``slab`` z-planes, same
+lateral extent, elements, transmits and frames), which has the same per-tile work.
 Results are cached per shape signature (dimensionality, grid, elements, transmits,
 frames, samples, storage type), so instances of the same shape are tuned once.
 """
@@ -23,17 +25,15 @@ def _signature(kw: dict) -> tuple:
 
 
 def _boxes(n: int, ndim: int) -> List[Tuple[int, int, int]]:
-    """Power-of-two voxel boxes of volume n."""
+    """Compact power-of-two voxel boxes of volume n (a few per lane mapping)."""
     out = []
     if ndim == 2:
-        x = 1
-        while x <= n:
-            if n % x == 0 and 2 <= x <= 64 and n // x <= 64:
+        for x in (4, 8, 16):
+            if n % x == 0 and n // x <= 64:
                 out.append((x, 1, n // x))
-            x *= 2
     else:
-        for x in (2, 4, 8, 16):
-            for y in (1, 2, 4, 8):
+        for x in (4, 8):
+            for y in (2, 4):
                 if n % (x * y) == 0 and 1 <= n // (x * y) <= 16:
                     out.append((x, y, n // (x * y)))
     return out
@@ -51,7 +51,15 @@ def candidates(kw: dict) -> List[Shape]:
     return cands
 
 
-def time_shape(kw: dict, shape: Shape, iq, y, pd, reps: int = 5) -> float:
+def _slab(kw: dict, planes: int) -> dict:
+    """The instance restricted to its first ``planes`` z-planes (regular grids only)."""
+    if kw.get("grid_dims") is None or kw["grid_dims"][2] <= planes:
+        return kw
+    nx, ny, nz = kw["grid_dims"]
+    return {**kw, "grid_dims": (nx, ny, planes)}
+
+
+def time_shape(kw: dict, shape: Shape, iq, y, pd, reps: int = 3) -> float:
     import torch
     with Batch([kw], shapes=[shape]) as b:
         b.bind([iq], [y], [pd])
@@ -68,14 +76,16 @@ def time_shape(kw: dict, shape: Shape, iq, y, pd, reps: int = 5) -> float:
     return statistics.median(ts)
 
 
-def tune_instance(kw: dict, iq, y, pd, max_candidates: Optional[int] = None) -> Tuple[Shape, Dict[Shape, float]]:
+def tune_instance(kw: dict, iq, y, pd, max_candidates: Optional[int] = None,
+                  slab: int = 16) -> Tuple[Shape, Dict[Shape, float]]:
     sig = _signature(kw)
     if sig in _CACHE:
         return _CACHE[sig], {}
     cands = candidates(kw)
     if max_candidates:
         cands = cands[:max_candidates]
-    times = {c: time_shape(kw, c, iq, y, pd) for c in cands}
+    small = _slab(kw, slab)          # y / pd are large enough for the slab (its voxels come first)
+    times = {c: time_shape(small, c, iq, y, pd) for c in cands}
     best = min(times, key=times.get)
     _CACHE[sig] = best
     return best, times

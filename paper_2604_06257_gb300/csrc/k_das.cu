@@ -247,6 +247,8 @@ const VariantShape kShapes[V_COUNT] = {
     {"staged_c64p_ft64_v4",        4, 16,   8,   64,  kWarps, false, true,  8, 8, 3},
     {"staged_f16_ft32_v4",         4,  8,  16,   32,  kWarps, false, true,  4, 4, 1},
     {"staged_b16_ft32_v4",         4,  8,  16,   32,  kWarps, false, true,  4, 4, 2},
+    {"staged_c64p_ft32_v4w7",      4,  8,  16,   32,  7,      false, true,  4, 8, 3, 8},
+    {"staged_c64_ft32_v4w7",       4,  8,  16,   32,  7,      false, true,  4, 8, 0, 8},
 };
 
 template <class K>

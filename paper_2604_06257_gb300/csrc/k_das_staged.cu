@@ -140,8 +140,9 @@ struct SlotMeta {
   float4 e;             // element position (sample units)
 };
 
-template <class IQ, int VEC, int NV, int FL, int VPG, int NWC, int NBUF, int MINB>
-__global__ void __launch_bounds__((NWC + 1) * 32) __maxnreg__(MINB == 2 ? 112 : (MINB == 3 ? 72 : (MINB == 4 ? 56 : (MINB == 5 ? 80 : 168)))) k_das_staged(const DasParams p) {
+// MAXR: register cap per thread, chosen so that the intended number of blocks fits per SM
+template <class IQ, int VEC, int NV, int FL, int VPG, int NWC, int NBUF, int MAXR>
+__global__ void __launch_bounds__((NWC + 1) * 32) __maxnreg__(MAXR) k_das_staged(const DasParams p) {
   constexpr int G = 32 / FL;
   constexpr int WV = G * VPG;
   constexpr int FPL = VEC * NV;
@@ -414,21 +415,23 @@ size_t staged_smem_bytes(Variant v, int rows_cap, int F, int T) {
 cudaError_t launch_das_staged(const DasParams& p, Variant v, cudaStream_t s) {
   const size_t sm = staged_smem_bytes(v, p.rows_cap, p.F, p.T);
   switch (v) {
-    case V_ST32_C64: return go_staged(k_das_staged<float2, 2, 2, 8, 8, 8, kRing, 2>, 8, p, sm, s);
-    case V_ST64_C64: return go_staged(k_das_staged<float2, 2, 2, 16, 8, 8, kRing, 2>, 8, p, sm, s);
-    case V_ST32_H16: return go_staged(k_das_staged<__half2, 4, 1, 8, 8, 8, kRing, 2>, 8, p, sm, s);
-    case V_ST64_H16: return go_staged(k_das_staged<__half2, 4, 1, 16, 8, 8, kRing, 2>, 8, p, sm, s);
-    case V_ST32_C64_V4: return go_staged(k_das_staged<float2, 2, 2, 8, 4, 8, kRing, 3>, 8, p, sm, s);
-    case V_ST32_C64_V4W4: return go_staged(k_das_staged<float2, 2, 2, 8, 4, 4, kRing, 5>, 4, p, sm, s);
-    case V_ST32_C64_V4R56: return go_staged(k_das_staged<float2, 2, 2, 8, 4, 8, kRing, 4>, 8, p, sm, s);
-    case V_ST32_C64P_V4: return go_staged(k_das_staged<C64Planar, 4, 1, 8, 4, 8, kRing, 3>, 8, p, sm, s);
-    case V_ST64_C64P_V4: return go_staged(k_das_staged<C64Planar, 4, 1, 16, 4, 8, 8, 3>, 8, p, sm, s);
-    case V_ST32_H16_V4: return go_staged(k_das_staged<__half2, 4, 1, 8, 4, 8, kRing, 3>, 8, p, sm, s);
-    case V_ST32_B16_V4: return go_staged(k_das_staged<__nv_bfloat162, 4, 1, 8, 4, 8, kRing, 3>, 8, p, sm, s);
-    case V_ST64_C64_V4: return go_staged(k_das_staged<float2, 2, 2, 16, 4, 8, 8, 3>, 8, p, sm, s);
-    case V_ST64_H16_V4: return go_staged(k_das_staged<__half2, 4, 1, 16, 4, 8, 8, 3>, 8, p, sm, s);
-    case V_ST32_B16: return go_staged(k_das_staged<__nv_bfloat162, 4, 1, 8, 8, 8, kRing, 2>, 8, p, sm, s);
-    case V_ST64_B16_V4: return go_staged(k_das_staged<__nv_bfloat162, 4, 1, 16, 4, 8, 8, 3>, 8, p, sm, s);
+    case V_ST32_C64: return go_staged(k_das_staged<float2, 2, 2, 8, 8, 8, kRing, 112>, 8, p, sm, s);
+    case V_ST64_C64: return go_staged(k_das_staged<float2, 2, 2, 16, 8, 8, kRing, 112>, 8, p, sm, s);
+    case V_ST32_H16: return go_staged(k_das_staged<__half2, 4, 1, 8, 8, 8, kRing, 112>, 8, p, sm, s);
+    case V_ST64_H16: return go_staged(k_das_staged<__half2, 4, 1, 16, 8, 8, kRing, 112>, 8, p, sm, s);
+    case V_ST32_C64_V4: return go_staged(k_das_staged<float2, 2, 2, 8, 4, 8, kRing, 72>, 8, p, sm, s);
+    case V_ST32_C64_V4W4: return go_staged(k_das_staged<float2, 2, 2, 8, 4, 4, kRing, 80>, 4, p, sm, s);
+    case V_ST32_C64_V4R56: return go_staged(k_das_staged<float2, 2, 2, 8, 4, 8, kRing, 56>, 8, p, sm, s);
+    case V_ST32_C64P_V4: return go_staged(k_das_staged<C64Planar, 4, 1, 8, 4, 8, kRing, 72>, 8, p, sm, s);
+    case V_ST64_C64P_V4: return go_staged(k_das_staged<C64Planar, 4, 1, 16, 4, 8, 8, 72>, 8, p, sm, s);
+    case V_ST32_C64P_V4W7: return go_staged(k_das_staged<C64Planar, 4, 1, 8, 4, 7, kRing, 64>, 7, p, sm, s);
+    case V_ST32_C64_V4W7: return go_staged(k_das_staged<float2, 2, 2, 8, 4, 7, kRing, 64>, 7, p, sm, s);
+    case V_ST32_H16_V4: return go_staged(k_das_staged<__half2, 4, 1, 8, 4, 8, kRing, 72>, 8, p, sm, s);
+    case V_ST32_B16_V4: return go_staged(k_das_staged<__nv_bfloat162, 4, 1, 8, 4, 8, kRing, 72>, 8, p, sm, s);
+    case V_ST64_C64_V4: return go_staged(k_das_staged<float2, 2, 2, 16, 4, 8, 8, 72>, 8, p, sm, s);
+    case V_ST64_H16_V4: return go_staged(k_das_staged<__half2, 4, 1, 16, 4, 8, 8, 72>, 8, p, sm, s);
+    case V_ST32_B16: return go_staged(k_das_staged<__nv_bfloat162, 4, 1, 8, 8, 8, kRing, 112>, 8, p, sm, s);
+    case V_ST64_B16_V4: return go_staged(k_das_staged<__nv_bfloat162, 4, 1, 16, 4, 8, 8, 72>, 8, p, sm, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -44,6 +44,8 @@ enum Variant : int32_t {
   V_ST64_C64P_V4,    // staged, 64-frame tile, split complex64 rows, 4 voxels per lane group
   V_ST32_H16_V4,     // staged, 32-frame tile, float16 pairs, 4 voxels per lane group
   V_ST32_B16_V4,     // staged, 32-frame tile, bfloat16 pairs, 4 voxels per lane group
+  V_ST32_C64P_V4W7,  // staged, split rows, 7 consumer warps, 64 registers: 4 blocks per SM
+  V_ST32_C64_V4W7,   // staged, interleaved, 7 consumer warps, 64 registers: 4 blocks per SM
   V_COUNT
 };
 
@@ -59,6 +61,7 @@ struct VariantShape {
   int ring_slots;
   int iq_bytes;          // bytes per complex sample
   int iq_type;           // mach_iq_dtype the variant reads
+  int tile2d_x;          // 2D tile width (0: squarest power-of-two split)
 };
 
 const VariantShape& variant_shape(Variant v);

@@ -152,12 +152,13 @@ Variant pick_variant(int iq_dtype, int F) {
 // The non-staged variant with the same frame tile (used when the ring would not fit).
 Variant unstaged(Variant v) {
   switch (v) {
-    case V_ST32_C64: case V_ST32_C64_V4: case V_ST32_C64_V4W4: case V_ST32_C64_V4R56: return V_F32_C64;
+    case V_ST32_C64: case V_ST32_C64_V4: case V_ST32_C64_V4W4: case V_ST32_C64_V4R56: case V_ST32_C64_V4W7:
+      return V_F32_C64;
     case V_ST64_C64: case V_ST64_C64_V4: return V_F64_C64;
     case V_ST32_H16: case V_ST32_H16_V4: return V_F32_H16;
     case V_ST64_H16: case V_ST64_H16_V4: return V_F64_H16;
     case V_ST32_B16: case V_ST32_B16_V4: return V_F32_B16;
-    case V_ST32_C64P_V4: return V_F32_C64P;
+    case V_ST32_C64P_V4: case V_ST32_C64P_V4W7: return V_F32_C64P;
     case V_ST64_C64P_V4: return V_F64_C64P;
     case V_ST64_B16_V4: return V_F64_B16;
     default: return v;
@@ -237,6 +238,11 @@ static mach_status configure_tiles(DasParams& b, Variant var, bool list, int64_t
   const int per_cta = shp.voxels_per_warp * shp.warps;
   int tile[3];
   pick_tile(per_cta, b.nx, b.ny, b.nz, list, tile);
+  if (shp.tile2d_x && !list && b.ny == 1 && b.nz > 1 && per_cta % shp.tile2d_x == 0) {
+    tile[0] = shp.tile2d_x;
+    tile[1] = 1;
+    tile[2] = per_cta / shp.tile2d_x;
+  }
   b.tile_x = tile[0];
   b.tile_y = tile[1];
   b.tile_z = tile[2];
@@ -249,21 +255,28 @@ static mach_status configure_tiles(DasParams& b, Variant var, bool list, int64_t
   // agree on which (element, transmit) pairs they use (the warp skips pairs none of them use)
   b.wb_x = b.wb_y = b.wb_z = 0;
   if (shp.staged && !list && !(b.ny == 1 && b.nz == 1)) {
-    int wb[3] = {0, 0, 0};
+    // candidate blocks, most compact first; the first one that divides the tile is used
+    static const int c2d32[][3] = {{8, 1, 4}, {16, 1, 2}, {4, 1, 8}};
+    static const int c2d16[][3] = {{4, 1, 4}, {8, 1, 2}, {16, 1, 1}};
+    static const int c2d8[][3] = {{4, 1, 2}, {8, 1, 1}};
+    static const int c3d32[][3] = {{4, 4, 2}, {8, 4, 1}};
+    static const int c3d16[][3] = {{4, 4, 1}, {8, 2, 1}};
+    static const int c3d8[][3] = {{4, 2, 1}, {8, 1, 1}};
     const int wv = shp.voxels_per_warp;
+    const int(*cand)[3] = nullptr;
+    int nc = 0;
     if (b.ny == 1) {
-      if (wv == 32) { wb[0] = 8; wb[1] = 1; wb[2] = 4; }
-      else if (wv == 16) { wb[0] = 4; wb[1] = 1; wb[2] = 4; }
-      else if (wv == 8) { wb[0] = 4; wb[1] = 1; wb[2] = 2; }
+      if (wv == 32) { cand = c2d32; nc = 3; } else if (wv == 16) { cand = c2d16; nc = 3; } else if (wv == 8) { cand = c2d8; nc = 2; }
     } else {
-      if (wv == 32) { wb[0] = 4; wb[1] = 4; wb[2] = 2; }
-      else if (wv == 16) { wb[0] = 4; wb[1] = 4; wb[2] = 1; }
-      else if (wv == 8) { wb[0] = 4; wb[1] = 2; wb[2] = 1; }
+      if (wv == 32) { cand = c3d32; nc = 2; } else if (wv == 16) { cand = c3d16; nc = 2; } else if (wv == 8) { cand = c3d8; nc = 2; }
     }
-    if (wb[0] && tile[0] % wb[0] == 0 && tile[1] % wb[1] == 0 && tile[2] % wb[2] == 0) {
-      b.wb_x = wb[0];
-      b.wb_y = wb[1];
-      b.wb_z = wb[2];
+    for (int k = 0; k < nc; ++k) {
+      if (tile[0] % cand[k][0] == 0 && tile[1] % cand[k][1] == 0 && tile[2] % cand[k][2] == 0) {
+        b.wb_x = cand[k][0];
+        b.wb_y = cand[k][1];
+        b.wb_z = cand[k][2];
+        break;
+      }
     }
   }
   if (b.frame_tiles > 65535) return MACH_ERR_UNSUPPORTED;   // grid y limit

@@ -47,14 +47,19 @@ __device__ __forceinline__ T ld(const T* p) {
 template <class IQ, int VEC, bool SMEM>
 __device__ __forceinline__ void load_vec(const IQ* p, float2 (&o)[VEC]) {
   if constexpr (std::is_same<IQ, float2>::value) {
+    static_assert(VEC == 1 || VEC == 2 || VEC == 4, "1, 2 or 4 samples");
     if constexpr (VEC == 1) {
       o[0] = ld<SMEM>(p);
     } else {
-      const float4 v = ld<SMEM>(reinterpret_cast<const float4*>(p));
-      o[0] = make_float2(v.x, v.y);
-      o[1] = make_float2(v.z, v.w);
+#pragma unroll
+      for (int h = 0; h < VEC / 2; ++h) {
+        const float4 v = ld<SMEM>(reinterpret_cast<const float4*>(p) + h);
+        o[2 * h] = make_float2(v.x, v.y);
+        o[2 * h + 1] = make_float2(v.z, v.w);
+      }
     }
   } else if constexpr (std::is_same<IQ, __half2>::value) {
+    static_assert(VEC == 1 || VEC == 4, "1 or 4 samples");
     if constexpr (VEC == 1) {
       o[0] = __half22float2(ld<SMEM>(p));
     } else {
@@ -65,6 +70,7 @@ __device__ __forceinline__ void load_vec(const IQ* p, float2 (&o)[VEC]) {
       o[3] = __half22float2(*reinterpret_cast<const __half2*>(&v.w));
     }
   } else {
+    static_assert(VEC == 1 || VEC == 4, "1 or 4 samples");
     if constexpr (VEC == 1) {
       o[0] = widen_bf16x2(ld<SMEM>(reinterpret_cast<const unsigned int*>(p)));
     } else {

@@ -13,6 +13,8 @@ Workloads (full scale):
   ``volume3d``  32 x 32 matrix, 11 plane waves, 64 frames, 1536 samples, 128^3 voxels
                 at 0.1 mm, F# 1.0 Gaussian; speckle (1 per (0.5 mm)^3) + 50 points at
                 30x rms; frames = static echo + independent noise at 30 dB (seed 3).
+  ``ulm3d``     3D ULM shape (Sec. 6): 32 x 32 matrix at 7.81 MHz, 5 plane waves, 32 frames,
+                94 x 94 x 178 voxels at 96 um; speckle + 200 microbubbles at 20x (seed 5).
 ``small`` scale keeps each workload's structure at sizes the FP64 oracle finishes
 in about a second, with grid sides that leave ragged tiles.
 """
@@ -24,7 +26,7 @@ import torch
 from . import acquisition, phantoms, iq as iqmod
 from .acquisition import Acquisition, bmode2d, doppler2d, volume3d, linear_array, matrix_array
 
-SEEDS = {"bmode2d": 1, "doppler2d": 2, "volume3d": 3}
+SEEDS = {"bmode2d": 1, "doppler2d": 2, "volume3d": 3, "ulm3d": 5}
 
 
 def make_acquisition(name: str, scale: str = "full", iq_dtype: str = "c64") -> Acquisition:
@@ -37,6 +39,10 @@ def make_acquisition(name: str, scale: str = "full", iq_dtype: str = "c64") -> A
             return doppler2d(iq_dtype=iq_dtype)
         return doppler2d(nx=61, nz=47, n_frames=32, iq_dtype=iq_dtype).replace(
             grid_origin=(-3.0e-3, 0.0, 18e-3))
+    if name == "ulm3d":
+        if scale == "full":
+            return acquisition.ulm3d(iq_dtype=iq_dtype)
+        return acquisition.ulm3d(n_frames=8, iq_dtype=iq_dtype, nx=13, ny=11, nz=17)
     if name == "volume3d":
         if scale == "full":
             return volume3d(iq_dtype=iq_dtype)
@@ -54,6 +60,9 @@ def make_phantom(name: str, acq: Acquisition, seed: int, scale: str = "full"):
     if name == "volume3d":
         per = 1.0 if scale == "full" else 4.0
         return phantoms.speckle_and_points(acq, seed, per_cell=per)
+    if name == "ulm3d":   # tissue speckle plus bright microbubbles
+        per = 0.5 if scale == "full" else 4.0
+        return phantoms.speckle_and_points(acq, seed, n_points=200, point_gain=20.0, per_cell=per)
     raise KeyError(name)
 
 
@@ -66,7 +75,7 @@ def make(name: str, scale: str = "full", device="cpu", seed=None, iq_dtype: str 
         iq = iqmod.simulate(acq, ph, seed=seed, snr_db=40.0, device=device)
     elif name == "doppler2d":
         iq = iqmod.simulate(acq, ph, seed=seed, snr_db=None, device=device)
-    else:
+    else:   # volume3d, ulm3d: static echo + independent noise per frame
         accum = torch.complex64 if scale == "full" else torch.complex128
         iq = iqmod.simulate(acq, ph, seed=seed, snr_db=30.0, device=device, accum=accum,
                             static_frames=True)

@@ -202,3 +202,23 @@ def pulse_sigma_samples(acq: Acquisition) -> float:
     full width at half maximum = 2 / fc."""
     fwhm = 2.0 / acq.fc
     return fwhm / (2.0 * math.sqrt(2.0 * math.log(2.0))) * acq.fs
+
+
+def ulm3d(n_frames: int = 32, iq_dtype: str = "c64", nx: int = 94, ny: int = 94, nz: int = 178) -> Acquisition:
+    """3D ultrasound-localisation-microscopy shape (Sec. 6): 32 x 32 matrix array
+    (pitch 0.3 mm) at 7.81 MHz, fs = 4 fc, five plane waves (broadside and +/-5 degrees in
+    azimuth and in elevation), a 94 x 94 x 178 grid at 96 um from 3 mm depth, F# 1.0
+    Gaussian window."""
+    ang = deg(0.0, -5.0, 5.0, 0.0, 0.0)
+    el = deg(0.0, 0.0, 0.0, -5.0, 5.0)
+    fc = 7.81e6
+    fs = 4 * fc
+    step = 96e-6
+    depth = 3e-3 + (nz - 1) * step
+    S = int(math.ceil(2.3 * depth * fs / 1540.0)) + 32
+    return Acquisition(
+        name=f"ulm3d_{nx}x{ny}x{nz}x{n_frames}", ndim=3, elem_pos=matrix_array(32, 32),
+        tx_angles=np.stack([ang, el], 1), fs=fs, fc=fc, c=1540.0, t0=0.0, f_number=1.0,
+        apod="gauss", n_samples=S, n_frames=n_frames, grid_dims=(nx, ny, nz),
+        grid_origin=(-(nx - 1) * step / 2, -(ny - 1) * step / 2, 3e-3),
+        grid_step=(step, step, step), iq_dtype=iq_dtype)

@@ -58,7 +58,7 @@ def check_terms(acq, plan, idx):
 
 # ------------------------------------------------------------------ tables ----
 
-@pytest.mark.parametrize("name", ["bmode2d", "doppler2d", "volume3d"])
+@pytest.mark.parametrize("name", ["bmode2d", "doppler2d", "volume3d", "ulm3d"])
 @pytest.mark.parametrize("scale", ["small", "full"])
 def test_tx_table_bit_identical(name, scale):
     acq = synth.make_acquisition(name, scale)
@@ -95,7 +95,7 @@ def test_terms_bit_exact_small(name):
     assert n > 0
 
 
-@pytest.mark.parametrize("name", ["bmode2d", "doppler2d", "volume3d"])
+@pytest.mark.parametrize("name", ["bmode2d", "doppler2d", "volume3d", "ulm3d"])
 def test_terms_bit_exact_full_sampled(name):
     acq = synth.make_acquisition(name, "full")
     idx = np.sort(np.random.default_rng(11).choice(acq.n_vox, 1500, replace=False))
@@ -132,7 +132,7 @@ def compare(acq, iq_host, y, pd, idx=None, bmode_db=FP32_BMODE_DB, iq_oracle=Non
     return out
 
 
-@pytest.mark.parametrize("name", ["bmode2d", "doppler2d", "volume3d"])
+@pytest.mark.parametrize("name", ["bmode2d", "doppler2d", "volume3d", "ulm3d"])
 def test_das_and_pd_small(name):
     acq, iq = synth.make(name, "small", device="cuda")
     with plan_for(acq) as p:
