@@ -475,7 +475,9 @@ def run_ragged(args):
             "config": {"workload": f"{len(acqs)} seeded instances: 2D 64-256 el / 128^2-384^2 px and 3D "
                                    f"256-1024 el / 64^3-112^3 voxels (grid scale {args.ragged_scale}), 1-48 "
                                    "frames, 1-15 transmits, log-uniform sizes (seed 4)",
-                       "points_per_step": points, "autotune_s": t_tune, "autotuned": shapes is not None},
+                       "points_per_step": points, "autotune_s": t_tune,
+                       "autotuned": shapes is not None,
+                       "note": "the autotuner keeps per-instance shapes only if the whole batch runs faster"},
             "batch_graph_autotuned": {"s": t_graph, "value": points / t_graph},
             "batch_autotuned": {"s": t_tuned, "value": points / t_tuned},
             **out,

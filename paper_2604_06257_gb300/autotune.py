@@ -77,7 +77,7 @@ def time_shape(kw: dict, shape: Shape, iq, y, pd, reps: int = 3) -> float:
 
 
 def tune_instance(kw: dict, iq, y, pd, max_candidates: Optional[int] = None,
-                  slab: int = 16) -> Tuple[Shape, Dict[Shape, float]]:
+                  slab: int = 32) -> Tuple[Shape, Dict[Shape, float]]:
     sig = _signature(kw)
     if sig in _CACHE:
         return _CACHE[sig], {}
@@ -85,11 +85,32 @@ def tune_instance(kw: dict, iq, y, pd, max_candidates: Optional[int] = None,
     if max_candidates:
         cands = cands[:max_candidates]
     small = _slab(kw, slab)          # y / pd are large enough for the slab (its voxels come first)
+    cands = [c for c in cands]
     times = {c: time_shape(small, c, iq, y, pd) for c in cands}
     best = min(times, key=times.get)
     _CACHE[sig] = best
     return best, times
 
 
-def tune_batch(instances: List[dict], iqs, ys, pds) -> List[Shape]:
-    return [tune_instance(kw, iq, y, pd)[0] for kw, iq, y, pd in zip(instances, iqs, ys, pds)]
+def time_batch(instances: List[dict], shapes, iqs, ys, pds, reps: int = 3) -> float:
+    import torch
+    with Batch(instances, shapes=shapes) as b:
+        b.bind(iqs, ys, pds)
+        b.run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            b.run()
+        e1.record()
+        e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def tune_batch(instances: List[dict], iqs, ys, pds) -> Optional[List[Shape]]:
+    """Per-instance choices, kept only if the whole batch runs faster with them than with
+    the library's default shapes (returns None in that case)."""
+    shapes = [tune_instance(kw, iq, y, pd)[0] for kw, iq, y, pd in zip(instances, iqs, ys, pds)]
+    if time_batch(instances, shapes, iqs, ys, pds) < time_batch(instances, None, iqs, ys, pds):
+        return shapes
+    return None

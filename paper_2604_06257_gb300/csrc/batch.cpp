@@ -110,6 +110,10 @@ mach_status mach_batch_plan(const mach_das_desc* descs, int32_t n, const mach_ti
     const bool list = descs[i].vox_pos != nullptr;
     int tile[3] = {sh.tile[0], sh.tile[1], sh.tile[2]};
     if (tile[0] == 0) pick_tile_shape(voxels_per_block(sh), p.nx, p.ny, p.nz, list, tile);
+    if (tile[0] * tile[1] * tile[2] != voxels_per_block(sh)) {
+      release(b);
+      return MACH_ERR_UNSUPPORTED;
+    }
     sh.tile[0] = tile[0];
     sh.tile[1] = tile[1];
     sh.tile[2] = tile[2];

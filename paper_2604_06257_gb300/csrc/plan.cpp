@@ -117,7 +117,7 @@ Variant pick_variant(int iq_dtype, int F) {
     if (F <= 4) return V_CH_C64;
     if (F % 2 == 0) {
       if (F <= 16) return V_F16_C64;
-      if (F <= 32) return V_ST32_C64_V4;
+      if (F <= 32) return V_ST32_C64_V4W7;
       if (F <= 64) return V_ST64_C64_V4;
       return V_F64_C64;
     }
@@ -125,7 +125,7 @@ Variant pick_variant(int iq_dtype, int F) {
   }
   if (iq_dtype == MACH_IQ_C64_SPLIT) {   // F % 4 == 0 and F > 4 (checked by validate)
     if (F <= 16) return V_F32_C64P;
-    if (F <= 32) return V_ST32_C64P_V4;
+    if (F <= 32) return V_ST32_C64P_V4W7;
     if (F <= 64) return V_ST64_C64P_V4;
     return V_F64_C64P;
   }
@@ -178,18 +178,23 @@ bool variant_accepts(Variant v, int iq_dtype, int F) {
 // Voxel tile of one block: compact boxes so that the voxels sharing a block (and the
 // L1 cache) read overlapping sample windows of each element.
 void pick_tile(int n, int nx, int ny, int nz, bool list, int tile[3]) {
+  // the box always holds exactly n voxel slots
   if (list || (ny == 1 && nz == 1)) {
     tile[0] = n; tile[1] = 1; tile[2] = 1;
     return;
   }
-  if (ny == 1) {   // 2D x-z grid: the squarest power-of-two split
+  if (ny == 1) {   // 2D x-z grid: the squarest power-of-two width that divides n
     int tx = 1;
     while (tx * tx < n) tx *= 2;
+    while (n % tx) tx /= 2;
     tile[0] = tx; tile[1] = 1; tile[2] = n / tx;
     return;
   }
-  int tx = 8, ty = 4;
-  if (n < 32) { tx = 4; ty = 2; }
+  // 3D: up to 8 along x and 4 along y (powers of two dividing n), the rest along z
+  int tx = 8;
+  while (n % tx) tx /= 2;
+  int ty = 4;
+  while ((n / tx) % ty) ty /= 2;
   tile[0] = tx; tile[1] = ty; tile[2] = n / (tx * ty);
 }
 
@@ -243,6 +248,7 @@ static mach_status configure_tiles(DasParams& b, Variant var, bool list, int64_t
     tile[1] = 1;
     tile[2] = per_cta / shp.tile2d_x;
   }
+  if (tile[0] * tile[1] * tile[2] != per_cta) return MACH_ERR_UNSUPPORTED;   // slots must map 1:1
   b.tile_x = tile[0];
   b.tile_y = tile[1];
   b.tile_z = tile[2];
