@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "DAS points/s (voxel x channel x transmit x frame, Eq. 1)"
 UNIT = "points/s"
 PAPER_POINTS_PER_S = 258_052_096 / 0.23e-3      # Sec. 4.2: 0.23 ms on an RTX 5090, 251^2 px
-KERNEL_SOURCES = ("k_das.cu", "k_das_staged.cu", "das_term.cuh", "async_copy.cuh", "mach_internal.h")
+KERNEL_SOURCES = ("k_das.cu", "k_das_staged.cu", "das_term.cuh", "tap_mac.cuh", "async_copy.cuh", "mach_internal.h")
 FLUSH_BYTES = 256 << 20                           # > 129 MB L2
 
 
