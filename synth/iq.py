@@ -140,3 +140,17 @@ def from_storage(x: torch.Tensor) -> torch.Tensor:
     if x.dtype == torch.float32 and x.dim() == 5 and x.shape[3] == 2:
         return torch.view_as_complex(x.permute(0, 1, 2, 4, 3).contiguous())
     return torch.view_as_complex(x.to(torch.float32).contiguous())
+
+
+def simulate_frames(acq: Acquisition, phantoms, device="cpu", chunk_elems: int = 1 << 26) -> torch.Tensor:
+    """IQ complex64 [T, C, S, F] whose frame f holds the noise-free echoes of
+    ``phantoms[f]`` (F = len(phantoms)): independent scenes carried on the frame axis."""
+    T, C, S, _ = acq.iq_shape
+    dev = torch.device(device)
+    out = torch.empty((T, C, S, len(phantoms)), dtype=torch.complex64, device=dev)
+    buf = torch.zeros((T, C, S), dtype=torch.complex64, device=dev)
+    for f, ph in enumerate(phantoms):
+        buf.zero_()
+        add_echoes(buf, acq, ph.static_pos, ph.static_amp, chunk_elems=chunk_elems)
+        out[..., f] = buf
+    return out

@@ -101,3 +101,51 @@ def speckle_and_points(acq: Acquisition, seed: int, n_points: int = 50,
     pp = lo + (hi - lo) * rng.random((n_points, 3))
     return Phantom(np.concatenate([pos, pp]),
                    np.concatenate([amp, np.full(n_points, point_gain)]))
+
+
+def compounding_base(acq: Acquisition, seed: int) -> Phantom:
+    """One building block of the learned-compounding training scenes (3D grids).
+
+    Kinds, drawn with probabilities 0.5 / 0.25 / 0.25:
+      * speckle patch: N(0, 1) scatterers at 4 per mm^3, uniform in a random box of
+        side 3-9 mm inside the grid;
+      * point cluster: 1-5 points of amplitude 5-30 anywhere in the grid;
+      * vessel: scatterers at 30 per mm^3 in a tube of radius 0.2-0.6 mm along a random
+        segment of length 4-12 mm, amplitudes N(0, 1) x 2.
+    Scenes are complex-weighted sums of such blocks; DAS is linear in the scatterer
+    amplitudes, so a scene's volume is the same weighted sum of the blocks' volumes.
+    """
+    rng = np.random.default_rng(seed)
+    lo, hi = _box(acq)
+    ext = hi - lo
+    kind = rng.random()
+    if kind < 0.5:
+        side = rng.uniform(3e-3, 9e-3, 3)
+        side = np.minimum(side, ext)
+        c0 = lo + (ext - side) * rng.random(3)
+        n = max(1, int(round(4.0 * np.prod(side) / 1e-9)))
+        pos = c0 + side * rng.random((n, 3))
+        return Phantom(pos, rng.standard_normal(n))
+    if kind < 0.75:
+        n = int(rng.integers(1, 6))
+        pos = lo + ext * rng.random((n, 3))
+        return Phantom(pos, rng.uniform(5.0, 30.0, n) * rng.choice([-1.0, 1.0], n))
+    radius = rng.uniform(0.2e-3, 0.6e-3)
+    length = rng.uniform(4e-3, 12e-3)
+    centre = lo + ext * rng.random(3)
+    d = rng.standard_normal(3)
+    d /= np.linalg.norm(d)
+    n = max(1, int(round(30.0 * math.pi * radius ** 2 * length / 1e-9)))
+    # uniform in the tube: position along the axis plus a uniform point of the disc
+    s = (rng.random(n) - 0.5) * length
+    u = np.cross(d, [1.0, 0.0, 0.0] if abs(d[0]) < 0.9 else [0.0, 1.0, 0.0])
+    u /= np.linalg.norm(u)
+    v = np.cross(d, u)
+    rr = radius * np.sqrt(rng.random(n))
+    th = 2 * math.pi * rng.random(n)
+    pos = centre + s[:, None] * d + (rr * np.cos(th))[:, None] * u + (rr * np.sin(th))[:, None] * v
+    keep = np.all((pos >= lo) & (pos <= hi), axis=1)
+    if not keep.any():
+        keep[:1] = True
+        pos[:1] = np.clip(pos[:1], lo, hi)
+    return Phantom(pos[keep], 2.0 * rng.standard_normal(int(keep.sum())))

@@ -18,10 +18,14 @@ def built():
     pkg_build.build()
 
 
-def declared_functions():
-    src = open(os.path.join(ROOT, "include", "mach.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(mach_[a-z0-9_]+)\s*\(", src)))
+def declared_functions(header=None):
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for h in sorted(os.listdir(inc)) if header is None else [header]:
+        src = open(os.path.join(inc, h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(mach_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported():
@@ -30,7 +34,9 @@ def test_every_declared_symbol_is_exported():
     assert "mach_das_plan" in names and "mach_power_doppler" in names
     for n in names:
         assert hasattr(L, n), n
-    assert set(m.EXPORTS) >= set(names)
+    assert set(m.EXPORTS) >= set(declared_functions("mach.h"))
+    from paper_2604_06257_gb300 import nn
+    assert set(m.EXPORTS) | set(nn.NN_EXPORTS) == set(names)
 
 
 def test_status_strings_and_version():
@@ -111,3 +117,28 @@ def test_valid_descriptor_without_gpu_reports_cuda_error():
     h = C.c_void_p()
     assert m.lib().mach_das_plan(C.byref(d), None, C.byref(h)) == m.MACH_ERR_CUDA
     assert h.value is None
+
+
+def test_network_entry_points_reject_bad_arguments_before_cuda():
+    from paper_2604_06257_gb300 import nn
+    L = nn._L()
+    fake = C.c_void_p(256)   # never dereferenced: every call below fails validation first
+    # channel counts must be multiples of 16
+    assert L.mach_nn_conv3d(fake, fake, None, fake, None, 1, 4, 4, 4, 8, 16, 0, 0, None) == m.MACH_ERR_INVALID_ARG
+    assert L.mach_nn_conv3d(fake, fake, None, None, None, 1, 4, 4, 4, 16, 16, 0, 0, None) == m.MACH_ERR_INVALID_ARG
+    assert L.mach_nn_conv3d(C.c_void_p(258), fake, None, fake, None, 1, 4, 4, 4, 16, 16, 0, 0, None) == \
+        m.MACH_ERR_INVALID_ARG   # misaligned input
+    assert L.mach_nn_conv3d_wgrad(fake, fake, fake, 1, 4, 4, 4, 16, 24, None) == m.MACH_ERR_INVALID_ARG
+    assert L.mach_nn_bias_grad(fake, fake, 10, 48, None) == m.MACH_ERR_INVALID_ARG
+    assert L.mach_nn_pool2(fake, fake, 1, 3, 4, 4, 16, 0, 0, None) == m.MACH_ERR_INVALID_ARG   # odd side
+    assert L.mach_nn_up2(fake, fake, 1, 2, 2, 2, 16, 16, 8, 0, None) == m.MACH_ERR_INVALID_ARG   # off + c > cy
+    assert L.mach_nn_adam(fake, fake, fake, fake, 10, 1e-3, 0.9, 0.999, 1e-8, 0, None, None, 0, 0, None) == \
+        m.MACH_ERR_INVALID_ARG   # step 0
+    h = C.c_void_p()
+    for d, want in [((0, 16, 1, 8, 8, 8), m.MACH_ERR_INVALID_ARG),      # no level
+                    ((4, 8, 1, 8, 8, 8), m.MACH_ERR_INVALID_ARG),       # base channels not a multiple of 16
+                    ((4, 16, 1, 12, 8, 8), m.MACH_ERR_INVALID_ARG),     # nx not a multiple of 8
+                    ((4, 16, 0, 8, 8, 8), m.MACH_ERR_INVALID_ARG),      # empty batch
+                    ((4, 48, 1, 8, 8, 8), m.MACH_ERR_UNSUPPORTED)]:     # 384 channels at the bottom
+        assert L.mach_unet_create(C.byref(nn.mach_unet_desc(*d)), 0, C.byref(h)) == want, d
+        assert not h.value

@@ -23,8 +23,9 @@ PD_DB = -60.0
 FP16_DB = -60.0
 # |y|^2 doubles the relative amplitude error of the stored samples: +6 dB over FP16_DB
 FP16_PD_DB = FP16_DB + 6.0
-# bfloat16 keeps 8 significand bits: unit roundoff 2^-9, rms rounding error 2^-9/sqrt(3)
-# ~ -59 dB of each sample; the gate leaves 9 dB of margin (PD: +6 dB as above)
+# bfloat16 keeps 8 significand bits (unit roundoff 2^-8): the rms relative rounding error of
+# a sample is about 2^-7/sqrt(12) x 0.72 (mean of 1/m over log-uniform mantissas m in [1, 2))
+# ~ -56 dB; the gate leaves 6 dB of margin (PD: +6 dB as above)
 BF16_DB = -50.0
 BF16_PD_DB = BF16_DB + 6.0
 
