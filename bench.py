@@ -485,6 +485,169 @@ def run_ragged(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------- learned compounding ----
+
+def run_learned(args):
+    """Learned compounding at 128^3 (matrix array, 1024 elements, 8 scenes per batch on the
+    frame axis): 3-angle DAS followed by the trained U-Net, against plain 21-angle DAS of
+    the same scenes.  Value = volumes/s of the learned path; both paths' errors against
+    the 21-angle volumes on held-out scenes are reported with it."""
+    import numpy as np
+    import torch
+    import oracle
+    from oracle import unet_oracle
+    import paper_2604_06257_gb300 as m
+    from paper_2604_06257_gb300 import build as pkg_build, learned as Lc
+    from paper_2604_06257_gb300.nn import UNet
+    from synth import phantoms
+    from synth.iq import simulate_frames
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
+    pkg_build.build()
+    m.lib()
+    n, B, nblk = 128, 8, 32
+    V = n ** 3
+    params, gain, levels, base = Lc.load(os.path.join(Lc.WEIGHTS_DIR, "unet_few3_many21_128.npz"))
+    # held-out scenes: blocks never used in training, complex-weighted, one scene per frame
+    acq_blk = Lc.acquisition(n, nblk, "many")
+    seeds = range(Lc.TEST_SEED0 + 5000, Lc.TEST_SEED0 + 5000 + nblk)
+    iq_blk = simulate_frames(acq_blk, [phantoms.compounding_base(acq_blk, s) for s in seeds], "cuda")
+    T, C, S, _ = iq_blk.shape
+    Wsc = torch.as_tensor(Lc.scene_weights(np.random.default_rng(99), nblk, B)).cuda()
+    iq = (iq_blk.view(-1, nblk) @ Wsc).view(T, C, S, B).contiguous()
+    del iq_blk
+    iq_few = iq.index_select(0, torch.tensor(Lc.FEW_IN_MANY, device="cuda")).contiguous()
+    acq_many, acq_few = Lc.acquisition(n, B, "many"), Lc.acquisition(n, B, "few")
+    pm, pf = m.Plan(**m.plan_kwargs(acq_many)), m.Plan(**m.plan_kwargs(acq_few))
+    net = UNet(n, n, n, B, levels=levels, base_ch=base)
+    net.set_params(params)
+    net.set_gain(gain)
+    y_many = torch.empty((V, B), dtype=torch.complex64, device="cuda")
+    y_few = torch.empty_like(y_many)
+    pred = torch.empty_like(y_many)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def plain():
+        pm.run(iq, y_many)
+
+    def learned():
+        pf.run(iq_few, y_few)
+        net.forward(y_few, pred)
+
+    def unet_only():
+        net.forward(y_few, pred)
+
+    plain()
+    learned()
+    torch.cuda.synchronize()
+    err = {"network_vs_21_angle_db": Lc.nrmse_db(pred, y_many),
+           "few_angle_ls_gain_vs_21_angle_db": Lc.nrmse_db(gain * y_few, y_many),
+           "target_db": -30.0, "scenes": B, "blocks": nblk,
+           "scenes_recipe": "complex-weighted sums of 6-16 seeded blocks (speckle patch / point cluster / "
+                            "vessel) never used in training"}
+
+    def timed(fn, steps):
+        for _ in range(max(3, args.warmup)):
+            flush.zero_()
+            fn()
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(b) for a, b in evs) / 1e3
+
+    steps = max(1, min(args.steps, 20))
+    clocks = Clocks(torch.cuda.get_device_properties(0).uuid.__str__())
+    clocks.start()
+    t_learned = timed(learned, steps)
+    t_plain = timed(plain, steps)
+    t_unet = timed(unet_only, steps)
+    clk = clocks.stop()
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("bf16_tflops", 1900.0)
+    achieved = net.flops_forward * B / t_unet / 1e12
+    L = levels
+    unet_launches = 2 + (L - 1) + 2 * L + 4 * (L - 1) + 2
+
+    # end to end through the public API: the 3-angle IQ from pinned host memory, the
+    # prediction back to pinned host memory, copies inside the timed region
+    iq_pin = iq_few.cpu().pin_memory()
+    out_pin = torch.empty((V, B), dtype=torch.complex64).pin_memory()
+    iq_dev = torch.empty_like(iq_few)
+
+    def e2e_step():
+        iq_dev.copy_(iq_pin, non_blocking=True)
+        pf.run(iq_dev, y_few)
+        net.forward(y_few, pred)
+        out_pin.copy_(pred, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    t_e2e = (time.perf_counter() - t0) / steps
+
+    # the oracle (FP64 C DAS + numpy U-Net) on one 64^3 sub-volume of one scene, scaled to
+    # whole volumes by the voxel count (both stages cost in proportion to the voxels)
+    cpu = None
+    if not args.no_cpu_baseline:
+        h = n // 2
+        sub = acq_few.replace(n_frames=1)
+        iq1 = iq_few[..., :1].contiguous().cpu()
+        g = np.arange(h) + h // 2
+        idx = (g[None, None, :] + n * (g[None, :, None] + n * g[:, None, None])).ravel()
+        t0 = time.perf_counter()
+        y1, _ = oracle.das(sub, iq1, idx)
+        t_das = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        unet_oracle.forward(params.astype(np.float64), y1, (h, h, h), levels, base, gain)
+        t_net = time.perf_counter() - t0
+        per_vol = (t_das + t_net) * (V / len(idx))
+        cpu = {"value": 1.0 / per_vol, "unit": "volumes/s", "cores": oracle.max_threads(), "kind": "oracle",
+               "sample": f"one 64^3 sub-volume of one scene: FP64 3-angle DAS {t_das:.1f} s + FP64 U-Net "
+                         f"{t_net:.1f} s, scaled by the voxel count ({V // len(idx)}x) to a 128^3 volume"}
+    line = {"metric": "compounded 128^3 volumes/s: 3-angle DAS + learned U-Net (vs plain 21-angle DAS)",
+            "value": B / t_learned, "unit": "volumes/s", "n_gpus": 1, "steps": steps, "warmup": max(3, args.warmup),
+            "ms_per_step": t_learned * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 DAS, bf16 U-Net (f32 accumulate)", "data": "synthetic",
+            "config": {"workload": f"learned compounding: 32x32 matrix array (1024 el, fc 7.8 MHz, fs 31.2 MHz), "
+                                   f"{n}^3 voxels at 0.1 mm, {B} scenes per batch, 3 plane waves "
+                                   "(az -10/0/10 deg) + U-Net (4 levels, 16-128 ch, 3x3x3, bf16) vs 21 plane "
+                                   "waves (az/el cross, -10..10 deg)",
+                       "l2": "flushed between timed steps (256 MB write, outside the timed events)",
+                       "weights": "unet_few3_many21_128.npz (trained by paper_2604_06257_gb300.learned)"},
+            "plain_21_angle": {"value": B / t_plain, "ms_per_step": t_plain * 1e3, "variant": pm.info()["variant"],
+                               "points_per_s": acq_many.points / t_plain},
+            "speedup_vs_plain": t_plain / t_learned,
+            "few_angle_das_ms": (t_learned - t_unet) * 1e3, "unet_forward_ms": t_unet * 1e3,
+            "error_db": err,
+            "roofline": {"bound": "tensor", "kernel": "U-Net forward (k_conv3d implicit GEMMs + elementwise)",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": None, "peak_source": "bf16 dense, MEASURED_PEAKS.json (burst)",
+                         "algorithmic": f"{net.flops_forward / 1e9:.1f} GFLOP per volume (2 x 27 x Cin x Cout "
+                                        "per voxel per convolution)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": B / t_e2e, "unit": "volumes/s",
+                    "h2d_bytes_per_step": iq_pin.numel() * iq_pin.element_size(),
+                    "d2h_bytes_per_step": out_pin.numel() * out_pin.element_size(), "steps": steps},
+            "gpu_launches": (1 + unet_launches) * steps, "clocks": clk}
+    print(json.dumps(line))
+    net.close()
+    pm.close()
+    pf.close()
+
+
 # ---------------------------------------------------------- reference arm ----
 
 def run_reference(args):
@@ -543,6 +706,8 @@ def main():
         run_reference(args)
     elif args.workload == "ragged":
         run_ragged(args)
+    elif args.workload == "learned3d":
+        run_learned(args)
     else:
         run_ours(args)
     try:

@@ -144,6 +144,15 @@ mach_status mach_iq_convert(const void *src_dev, int32_t src_order, void *dst_de
                             void *stream);
 
 /* Release a plan and its device tables (synchronises the device).  NULL is a no-op. */
+/* Uncompounded output (the output shape of the paper's memory table, Table 3: voxels x
+ * compounded planes x frames): y_dev complex64 [n_vox][n_tx][n_frames], element
+ * (v, t, f) = the delay-and-sum of transmit t alone, i.e. the terms of transmit t of
+ * mach_das_run's sum (Sec. 2.1 before the coherent compounding over transmits).  One
+ * launch per transmit on `stream`; same IQ layout, alignment and errors as mach_das_run
+ * (MACH_ERR_UNSUPPORTED if a transmit's slice of an output row would break the vector
+ * alignment the plan's kernel uses). */
+mach_status mach_das_run_per_tx(mach_plan p, const void *iq_dev, void *y_dev, void *stream);
+
 mach_status mach_plan_destroy(mach_plan p);
 
 /* Static, NUL-terminated description of a status code. */

@@ -58,6 +58,27 @@ mach_status mach_nn_conv3d(const void* x, const void* w, const float* bias, void
                            int32_t n, int32_t nz, int32_t ny, int32_t nx, int32_t ci, int32_t co,
                            int32_t flip, int32_t act, void* stream);
 
+/* The same convolution on the 5th-generation tensor cores (tcgen05.mma, accumulator in
+ * tensor memory, operands staged by TMA): w_packed is the output of mach_nn_pack_weights
+ * for this direction (the forward copy, or the flipped copy with flip != 0, in which case
+ * ci / co are the flipped convolution's input / output channels).  ci, co multiples of
+ * 16, co <= 256.  MACH_ERR_UNSUPPORTED if the driver offers no tensor-map encoder.  A
+ * bounded wait that gives up is reported by mach_nn_device_status. */
+mach_status mach_nn_conv3d_tc(const void* x, const void* w_packed, const float* bias, void* y, float* y_f32,
+                              int32_t n, int32_t nz, int32_t ny, int32_t nx, int32_t ci, int32_t co,
+                              int32_t flip, int32_t act, void* stream);
+
+/* float32 weights [27][ci][co] -> bfloat16 copies in the tensor-core layout: w_packed
+ * [ci/16][27][2][co][8] (element (kc, t, g, o, j) = W[t][16kc + 8g + j][o]) for the
+ * forward convolution and w_packed_flip [co/16][27][2][ci][8] (= W[t][i][16kc + 8g + j])
+ * for its data gradient; either output may be NULL. */
+mach_status mach_nn_pack_weights(const float* w, void* w_packed, void* w_packed_flip, int32_t ci, int32_t co,
+                                 void* stream);
+
+/* Synchronises `stream` and returns MACH_ERR_TIMEOUT (clearing it) if a tensor-core
+ * convolution gave up a bounded wait since the last call, else MACH_OK. */
+mach_status mach_nn_device_status(void* stream);
+
 /* Weight gradient, accumulated:  dw[tap, ci, co] += sum_{n,z,y,x} X[n, z+dz, y+dy, x+dx, ci] *
  * dY[n, z, y, x, co]   (float32 dw, caller zeroes it). */
 mach_status mach_nn_conv3d_wgrad(const void* x, const void* dy, float* dw, int32_t n, int32_t nz, int32_t ny,
@@ -129,6 +150,10 @@ mach_status mach_unet_set_params(mach_unet net, const float* host, int64_t count
 /* Gradients of the last mach_unet_backward, same order as the parameters. */
 mach_status mach_unet_get_grads(mach_unet net, float* host, int64_t count);
 mach_status mach_unet_set_gain(mach_unet net, float gain);
+/* Convolution kernels: MACH_UNET_TCGEN05 (default) or MACH_UNET_MMA_SYNC (warp-level
+ * mma.sync implicit GEMM, kept for comparison). */
+typedef enum { MACH_UNET_TCGEN05 = 0, MACH_UNET_MMA_SYNC = 1 } mach_unet_backend;
+mach_status mach_unet_set_backend(mach_unet net, int32_t backend);
 
 /* Prediction for `batch` input volumes: x, y complex64 [V][batch] device (y may not
  * alias x). */

@@ -32,7 +32,7 @@ EXPORTS = ("mach_das_plan", "mach_das_run", "mach_power_doppler", "mach_plan_des
            "mach_version", "mach_debug_fail_alloc_after", "mach_plan_device_status",
            "mach_debug_force_variant", "mach_debug_set_wait_limit", "mach_debug_stall_producer",
            "mach_das_run_noalloc", "mach_iq_convert", "mach_batch_plan", "mach_batch_bind",
-           "mach_batch_run", "mach_batch_get_info", "mach_batch_destroy")
+           "mach_batch_run", "mach_batch_get_info", "mach_batch_destroy", "mach_das_run_per_tx")
 
 
 class MachError(RuntimeError):
@@ -94,6 +94,8 @@ def lib():
         vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
         L.mach_das_plan.argtypes = [C.POINTER(mach_das_desc), vp, C.POINTER(vp)]
         L.mach_das_run.argtypes = [vp, vp, vp, vp]
+        L.mach_das_run_per_tx.argtypes = [vp, vp, vp, vp]
+        L.mach_das_run_per_tx.restype = C.c_int
         L.mach_power_doppler.argtypes = [vp, vp, vp, vp, vp]
         L.mach_plan_destroy.argtypes = [vp]
         L.mach_status_string.argtypes = [C.c_int]
@@ -258,6 +260,13 @@ def mach_das_run(plan: int, iq, y, stream=None) -> None:
         raise MachError(st, "mach_das_run")
 
 
+def mach_das_run_per_tx(plan: int, iq, y, stream=None) -> None:
+    """Uncompounded frames y [V, T, F] complex64 (one volume per transmit)."""
+    st = lib().mach_das_run_per_tx(plan, _dev_ptr(iq, "iq"), _dev_ptr(y, "y"), _stream_ptr(stream))
+    if st != MACH_OK:
+        raise MachError(st, "mach_das_run_per_tx")
+
+
 def mach_power_doppler(plan: int, iq, pd, y=None, stream=None) -> None:
     st = lib().mach_power_doppler(plan, _dev_ptr(iq, "iq"), _dev_ptr(pd, "pd"), _dev_ptr(y, "y"),
                                   _stream_ptr(stream))
@@ -410,6 +419,16 @@ class Plan:
                                                                 dtype=torch.complex64, device=iq.device))
         mach_das_run(self.handle, iq, out, stream)
         return out.cpu() if host else out
+
+    def run_per_tx(self, iq, y=None, stream=None):
+        """Uncompounded frames y [V, T, F] (complex64), CUDA tensors only."""
+        torch = self._torch
+        self._check_iq(iq)
+        T = self.iq_shape[0]
+        out = y if y is not None else torch.empty((self.n_vox, T, self.n_frames), dtype=torch.complex64,
+                                                  device=iq.device)
+        mach_das_run_per_tx(self.handle, iq, out, stream)
+        return out
 
     def power_doppler(self, iq, pd=None, y=None, want_y=False, stream=None):
         """Power Doppler pd [V] (float32) and, if requested, the frames y [V, F]."""

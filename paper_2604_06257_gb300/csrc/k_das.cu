@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_das_frames(const DasParams p) {
           const float2 a = acc_frame<IQ, VEC>(&acc[k][m * VEC], e);
           pw = fmaf(a.x, a.x, fmaf(a.y, a.y, pw));
         }
-        if (v >= 0 && p.y) store_y<IQ, VEC>(p.y + v * p.F + f, &acc[k][m * VEC]);
+        if (v >= 0 && p.y) store_y<IQ, VEC>(p.y + v * p.ystride + f, &acc[k][m * VEC]);
       }
     }
 #pragma unroll
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_das_channels(const DasParams p) 
     for (int f = 0; f < FMAX; ++f) {
       if (f < p.F) {
         pw = fmaf(acc[f].x, acc[f].x, fmaf(acc[f].y, acc[f].y, pw));
-        if (p.y) p.y[v * p.F + f] = acc[f];
+        if (p.y) p.y[v * p.ystride + f] = acc[f];
       }
     }
     if (p.pd) p.pd[v] = pw;

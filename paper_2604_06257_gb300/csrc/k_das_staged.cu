@@ -196,7 +196,7 @@ __global__ void __launch_bounds__((NWC + 1) * 32) __maxnreg__(MAXR) k_das_staged
         c = pi / p.T;
         t = pi - c * p.T;
         e = __ldg(&p.elem[c]);
-        use = pair_window(blo, bhi, __ldg(&p.txr[tile * p.T + t]), e, p, lo, rows);
+        use = pair_window(blo, bhi, __ldg(&p.txr[tile * p.txr_stride + t]), e, p, lo, rows);
         rows = min(rows, p.rows_cap);
       }
       unsigned todo = __ballot_sync(0xffffffffu, use);
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__((NWC + 1) * 32) __maxnreg__(MAXR) k_das_staged
           pw = fmaf(a.x, a.x, fmaf(a.y, a.y, pw));
         }
         if (v >= 0 && p.y) {
-          float2* dst = p.y + v * p.F + f;
+          float2* dst = p.y + v * p.ystride + f;
 #pragma unroll
           for (int e = 0; e < VEC; e += 2) {
             const float2 a = acc_frame<IQ, VEC>(&acc[k][mm * VEC], e), b = acc_frame<IQ, VEC>(&acc[k][mm * VEC], e + 1);

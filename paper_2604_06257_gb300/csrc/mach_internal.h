@@ -72,11 +72,12 @@ struct DasParams {
   const float4* elem;   // [C] element position in sample units
   const float* tx;      // [T][V] transmit delay in samples
   const void* iq;       // [T][C][S][F] complex (float2 or half2)
-  float2* y;            // [V][F] or nullptr
+  float2* y;            // [V][F] or nullptr (row of voxel v at y + v * ystride)
   float* pd;            // [V] or nullptr
   float* pd_part;       // [frame_tiles][V] scratch when frame_tiles > 1
   int64_t V;
   int C, T, S, F;
+  int64_t ystride;      // complex elements between consecutive voxels' output rows (F)
   int nx, ny, nz;       // voxel index space (a list is nx = V, ny = nz = 1)
   int tile_x, tile_y, tile_z;
   int tiles_x, tiles_y, tiles_z;
@@ -92,7 +93,8 @@ struct DasParams {
   int frame_tiles;
   // staged variants only
   const float4* tbox;   // [tiles][2] voxel bounding box of each tile (sample units)
-  const float2* txr;    // [tiles][T] (min, max) transmit delay over each tile
+  const float2* txr;    // [tiles][txr_stride] (min, max) transmit delay over each tile
+  int txr_stride;       // transmits per tile row of txr (T; larger for a single-transmit run)
   int rows_cap;         // rows of one ring slot
   uint32_t wait_limit;  // polls before a wait gives up
   int* err;             // device error word (bit 0: a wait timed out)

@@ -24,6 +24,12 @@ cudaError_t launch_loss(const float* o, const float* xf, const float2* target, c
 cudaError_t launch_output(const float* o, const float* xf, const float* sums, float gain, int64_t V, int N, int C,
                           float2* y, cudaStream_t s);
 
+// tensor-core convolution (k_conv_tc.cu); cudaErrorNotSupported without a tensor-map encoder
+bool conv_tc_supported(int ci, int co);
+cudaError_t launch_conv_tc(const void* x, const void* wpk, const float* bias, void* y, float* yf, int n, int d,
+                           int h, int w, int ci, int co, int flip, int act, cudaStream_t s);
+cudaError_t launch_pack_weights(const float* w, void* wpk, void* wpkt, int ci, int co, cudaStream_t s);
+
 // bfloat16 copies of float32 weights [27][ci][co]: wb (same layout) and wbt ([27][co][ci])
 cudaError_t launch_to_bf16(const float* w, int64_t count, void* wb, void* wbt, int ci, int co, cudaStream_t s);
 

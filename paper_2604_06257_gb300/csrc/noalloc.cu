@@ -167,6 +167,8 @@ extern "C" mach_status mach_das_run_noalloc(const mach_das_desc* d, const void* 
   b.T = T;
   b.S = S;
   b.F = F;
+  b.ystride = F;
+  b.txr_stride = T;
   b.apod = d->apod;
   b.two_f = static_cast<float>(2.0 * d->f_number);
   b.f_num = static_cast<float>(d->f_number);

@@ -423,6 +423,8 @@ mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) 
   b.T = T;
   b.S = S;
   b.F = F;
+  b.ystride = F;
+  b.txr_stride = T;
   b.apod = d->apod;
   b.two_f = static_cast<float>(2.0 * d->f_number);
   b.f_num = static_cast<float>(d->f_number);
@@ -521,6 +523,33 @@ static mach_status run(mach_plan p, const void* iq, float* pd, void* y, void* st
 mach_status mach_das_run(mach_plan p, const void* iq_dev, void* y_dev, void* stream) {
   if (!y_dev) return MACH_ERR_INVALID_ARG;
   return run(p, iq_dev, nullptr, y_dev, stream);
+}
+
+mach_status mach_das_run_per_tx(mach_plan p, const void* iq_dev, void* y_dev, void* stream) {
+  if (!p || !iq_dev || !y_dev) return MACH_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(iq_dev) & 15u) || (reinterpret_cast<uintptr_t>(y_dev) & 15u))
+    return MACH_ERR_INVALID_ARG;
+  const DasParams& b = p->base;
+  const int T = b.T, F = b.F;
+  // bytes of one transmit's IQ block [C][S][F] (split rows hold the same values)
+  const size_t sample_bytes = (p->d.iq_dtype == MACH_IQ_F16X2 || p->d.iq_dtype == MACH_IQ_BF16X2) ? 4 : 8;
+  const size_t tx_bytes = sample_bytes * static_cast<size_t>(b.C) * b.S * F;
+  // vector stores need each transmit's slice of a row on the same alignment as the row
+  const int vec = F % 4 == 0 ? 4 : (F % 2 == 0 ? 2 : 1);
+  if ((static_cast<int64_t>(T) * F) % vec) return MACH_ERR_UNSUPPORTED;
+  for (int t = 0; t < T; ++t) {
+    DasParams q = b;
+    q.T = 1;
+    q.tx = b.tx + static_cast<size_t>(t) * b.V;
+    q.txr = b.txr ? b.txr + t : nullptr;
+    q.iq = static_cast<const char*>(iq_dev) + t * tx_bytes;
+    q.y = static_cast<float2*>(y_dev) + static_cast<size_t>(t) * F;
+    q.ystride = static_cast<int64_t>(T) * F;
+    q.pd = nullptr;
+    const cudaError_t e = launch_das(q, p->variant, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return MACH_ERR_CUDA;
+  }
+  return MACH_OK;
 }
 
 mach_status mach_power_doppler(mach_plan p, const void* iq_dev, float* pd_dev, void* y_dev_or_null,

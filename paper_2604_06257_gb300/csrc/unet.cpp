@@ -30,6 +30,8 @@ struct Conv {
   int64_t w_off = 0, b_off = 0;
   void* wb = nullptr;   // bfloat16 [27][ci][co]
   void* wbt = nullptr;  // bfloat16 [27][co][ci]
+  void* wpk = nullptr;  // bfloat16, tensor-core layout of the forward convolution
+  void* wpkt = nullptr; // bfloat16, tensor-core layout of the data-gradient convolution
 };
 
 uint64_t splitmix64(uint64_t z) {
@@ -69,6 +71,7 @@ struct mach_unet_s {
   size_t arena_bytes = 0;
   float gain = 1.f;
   int step = 0;
+  int backend = MACH_UNET_TCGEN05;
 
   int ch(int l) const { return c0 << l; }
   int64_t vox(int l) const { return static_cast<int64_t>(N) * nz[l] * ny[l] * nx[l]; }
@@ -91,6 +94,10 @@ mach_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? MACH_OK : MACH_ER
 
 mach_status conv_fwd(mach_unet_s* u, const Conv& c, cudaStream_t s) {
   const int l = c.level;
+  if (u->backend == MACH_UNET_TCGEN05)
+    return cuda_ok(launch_conv_tc(c.in->p, c.wpk, u->params + c.b_off, c.out ? c.out->p : nullptr,
+                                  c.out ? nullptr : u->o, u->N, u->nz[l], u->ny[l], u->nx[l], c.ci, c.co, 0,
+                                  c.act ? 1 : 0, s));
   return mach_nn_conv3d(c.in->p, c.wb, u->params + c.b_off, c.out ? c.out->p : nullptr, c.out ? nullptr : u->o, u->N,
                         u->nz[l], u->ny[l], u->nx[l], c.ci, c.co, 0, c.act ? 1 : 0, s);
 }
@@ -100,7 +107,10 @@ mach_status conv_bwd(mach_unet_s* u, const Conv& c, void* gout, void* gin, cudaS
   const int l = c.level;
   TRY(mach_nn_conv3d_wgrad(c.in->p, gout, u->grads + c.w_off, u->N, u->nz[l], u->ny[l], u->nx[l], c.ci, c.co, s));
   TRY(mach_nn_bias_grad(gout, u->grads + c.b_off, u->vox(l), c.co, s));
-  if (gin)
+  if (gin && u->backend == MACH_UNET_TCGEN05)
+    TRY(cuda_ok(launch_conv_tc(gout, c.wpkt, nullptr, gin, nullptr, u->N, u->nz[l], u->ny[l], u->nx[l], c.co, c.ci,
+                               1, 0, s)));
+  else if (gin)
     TRY(mach_nn_conv3d(gout, c.wbt, nullptr, gin, nullptr, u->N, u->nz[l], u->ny[l], u->nx[l], c.co, c.ci, 1, 0, s));
   return MACH_OK;
 }
@@ -158,8 +168,10 @@ mach_status backward(mach_unet_s* u, const void* target, float* loss, cudaStream
 }
 
 mach_status refresh_bf16(mach_unet_s* u, cudaStream_t s) {
-  for (const Conv& c : u->convs)
+  for (const Conv& c : u->convs) {
     TRY(cuda_ok(launch_to_bf16(u->params + c.w_off, 27LL * c.ci * c.co, c.wb, c.wbt, c.ci, c.co, s)));
+    TRY(cuda_ok(launch_pack_weights(u->params + c.w_off, c.wpk, c.wpkt, c.ci, c.co, s)));
+  }
   return MACH_OK;
 }
 
@@ -267,6 +279,8 @@ mach_status mach_unet_create(const mach_unet_desc* desc, uint64_t seed, mach_une
   for (Conv& c : u->convs) {
     want(&c.wb, 2 * 27 * static_cast<size_t>(c.ci) * c.co);
     want(&c.wbt, 2 * 27 * static_cast<size_t>(c.ci) * c.co);
+    want(&c.wpk, 2 * 27 * static_cast<size_t>(c.ci) * c.co);
+    want(&c.wpkt, 2 * 27 * static_cast<size_t>(c.ci) * c.co);
   }
   auto want_act = [&](Act& t) { want(&t.p, 2 * static_cast<size_t>(u->vox(t.level)) * t.C); };
   for (int l = 0; l < L; ++l) {
@@ -366,6 +380,12 @@ mach_status mach_unet_set_params(mach_unet net, const float* host, int64_t count
   return cuda_ok(cudaDeviceSynchronize());
 }
 
+mach_status mach_unet_set_backend(mach_unet net, int32_t backend) {
+  if (!net || (backend != MACH_UNET_TCGEN05 && backend != MACH_UNET_MMA_SYNC)) return MACH_ERR_INVALID_ARG;
+  net->backend = backend;
+  return MACH_OK;
+}
+
 mach_status mach_unet_set_gain(mach_unet net, float gain) {
   if (!net || !std::isfinite(gain)) return MACH_ERR_INVALID_ARG;
   net->gain = gain;
@@ -394,10 +414,12 @@ mach_status mach_unet_train_step(mach_unet net, const void* x, const void* targe
   TRY(forward(net, x, s));
   TRY(backward(net, target, loss, s));
   ++net->step;
+  const bool tc = net->backend == MACH_UNET_TCGEN05;
   for (const Conv& c : net->convs) {
     const int64_t nw = 27LL * c.ci * c.co;
     TRY(mach_nn_adam(net->params + c.w_off, net->adam_m + c.w_off, net->adam_v + c.w_off, net->grads + c.w_off, nw,
-                     lr, 0.9f, 0.999f, 1e-8f, net->step, c.wb, c.wbt, c.ci, c.co, s));
+                     lr, 0.9f, 0.999f, 1e-8f, net->step, tc ? nullptr : c.wb, tc ? nullptr : c.wbt, c.ci, c.co, s));
+    if (tc) TRY(cuda_ok(launch_pack_weights(net->params + c.w_off, c.wpk, c.wpkt, c.ci, c.co, s)));
     TRY(mach_nn_adam(net->params + c.b_off, net->adam_m + c.b_off, net->adam_v + c.b_off, net->grads + c.b_off, c.co,
                      lr, 0.9f, 0.999f, 1e-8f, net->step, nullptr, nullptr, 0, 0, s));
   }

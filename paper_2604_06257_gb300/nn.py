@@ -14,7 +14,8 @@ import numpy as np
 
 from . import MachError, _dev_ptr, _stream_ptr, lib
 
-NN_EXPORTS = ("mach_nn_conv3d", "mach_nn_conv3d_wgrad", "mach_nn_bias_grad", "mach_nn_lrelu_bwd",
+NN_EXPORTS = ("mach_nn_conv3d", "mach_nn_conv3d_tc", "mach_nn_pack_weights", "mach_nn_device_status",
+              "mach_unet_set_backend", "mach_nn_conv3d_wgrad", "mach_nn_bias_grad", "mach_nn_lrelu_bwd",
               "mach_nn_pool2", "mach_nn_up2", "mach_nn_copy_channels", "mach_nn_adam",
               "mach_unet_create", "mach_unet_destroy", "mach_unet_get_info", "mach_unet_get_params",
               "mach_unet_set_params", "mach_unet_get_grads", "mach_unet_set_gain", "mach_unet_forward",
@@ -41,6 +42,10 @@ def _L():
         vp, i32, i64, f32 = C.c_void_p, C.c_int32, C.c_int64, C.c_float
         sig = {
             "mach_nn_conv3d": [vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, i32, i32, i32, vp],
+            "mach_nn_conv3d_tc": [vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, i32, i32, i32, vp],
+            "mach_nn_pack_weights": [vp, vp, vp, i32, i32, vp],
+            "mach_nn_device_status": [vp],
+            "mach_unet_set_backend": [vp, i32],
             "mach_nn_conv3d_wgrad": [vp, vp, vp, i32, i32, i32, i32, i32, i32, vp],
             "mach_nn_bias_grad": [vp, vp, i64, i32, vp],
             "mach_nn_lrelu_bwd": [vp, vp, i64, vp],
@@ -91,6 +96,31 @@ def mach_nn_conv3d(x, w, bias, y, y_f32, flip=False, act=False, stream=None):
     _check(_L().mach_nn_conv3d(_bf16(x, "x"), _bf16(w, "w"), _f32(bias, "bias"), _bf16(y, "y"),
                                _f32(y_f32, "y_f32"), N, nz, ny, nx, ci, co, int(flip), int(act),
                                _stream_ptr(stream)), "mach_nn_conv3d")
+
+
+def mach_nn_pack_weights(w, ci, co, forward=True, flipped=True, stream=None):
+    """float32 weights [27, ci, co] -> (forward, flipped) bfloat16 copies in the
+    tensor-core layout (flat tensors; None where not requested)."""
+    import torch
+    n = 27 * ci * co
+    wpk = torch.empty(n, dtype=torch.bfloat16, device=w.device) if forward else None
+    wpkt = torch.empty(n, dtype=torch.bfloat16, device=w.device) if flipped else None
+    _check(_L().mach_nn_pack_weights(_f32(w, "w"), _bf16(wpk, "wpk"), _bf16(wpkt, "wpkt"), ci, co,
+                                     _stream_ptr(stream)), "mach_nn_pack_weights")
+    return wpk, wpkt
+
+
+def mach_nn_conv3d_tc(x, w_packed, co, bias, y, y_f32, flip=False, act=False, stream=None):
+    """Tensor-core convolution: x bf16 [N, nz, ny, nx, ci], w_packed from mach_nn_pack_weights
+    (the flipped copy when flip), outputs [N, nz, ny, nx, co]."""
+    N, nz, ny, nx, ci = x.shape
+    _check(_L().mach_nn_conv3d_tc(_bf16(x, "x"), _bf16(w_packed, "w_packed"), _f32(bias, "bias"), _bf16(y, "y"),
+                                  _f32(y_f32, "y_f32"), N, nz, ny, nx, ci, co, int(flip), int(act),
+                                  _stream_ptr(stream)), "mach_nn_conv3d_tc")
+
+
+def mach_nn_device_status(stream=None) -> int:
+    return int(_L().mach_nn_device_status(_stream_ptr(stream)))
 
 
 def mach_nn_conv3d_wgrad(x, dy, dw, stream=None):
@@ -202,6 +232,11 @@ class UNet:
         out = np.empty(self.n_params, dtype=np.float32)
         _check(_L().mach_unet_get_grads(self.handle, out.ctypes.data, self.n_params), "mach_unet_get_grads")
         return out
+
+    def set_backend(self, backend: str) -> None:
+        """'tcgen05' (default) or 'mma.sync'."""
+        _check(_L().mach_unet_set_backend(self.handle, {"tcgen05": 0, "mma.sync": 1}[backend]),
+               "mach_unet_set_backend")
 
     def set_gain(self, gain: float) -> None:
         _check(_L().mach_unet_set_gain(self.handle, float(gain)), "mach_unet_set_gain")

@@ -84,6 +84,78 @@ def test_conv3d_flip_is_the_data_gradient(ci, co, shape):
     assert np.all(np.abs(got - ref) <= bound)
 
 
+TC_CASES = CONV_CASES + [(16, 16, (2, 16, 64, 64)), (32, 128, (2, 4, 40, 24)), (16, 256, (1, 3, 17, 9))]
+
+
+def test_packed_weight_layouts():
+    nn = _nn()
+    r = np.random.default_rng(5)
+    ci, co = 48, 32
+    w = torch.as_tensor(r.standard_normal((27, ci, co)).astype(np.float32)).to(dev)
+    wpk, wpkt = nn.mach_nn_pack_weights(w, ci, co)
+    wb = w.to(torch.bfloat16)
+    # forward: [ci/16][27][2][co][8], element (kc, t, g, o, j) = W[t][16kc + 8g + j][o]
+    ref = wb.view(27, ci // 16, 2, 8, co).permute(1, 0, 2, 4, 3).reshape(-1)
+    assert torch.equal(wpk, ref)
+    # flipped: [co/16][27][2][ci][8], element (kc, t, g, i, j) = W[t][i][16kc + 8g + j]
+    ref = wb.view(27, ci, co // 16, 2, 8).permute(2, 0, 3, 1, 4).reshape(-1)
+    assert torch.equal(wpkt, ref)
+
+
+@pytest.mark.parametrize("ci,co,shape", TC_CASES)
+@pytest.mark.parametrize("act", [False, True])
+def test_conv3d_tcgen05_forward(ci, co, shape, act):
+    nn = _nn()
+    r = np.random.default_rng(ci * 1000 + co + 17)
+    x, xh = _bf(r.standard_normal(shape + (ci,)))
+    w32 = (r.standard_normal((27, ci, co)) * np.sqrt(2.0 / (27 * ci))).astype(np.float32)
+    w, wh = _bf(w32)
+    wpk, _ = nn.mach_nn_pack_weights(w.float(), ci, co, flipped=False)
+    b = torch.as_tensor(r.standard_normal(co).astype(np.float32)).to(dev)
+    y = torch.empty(shape + (co,), dtype=torch.bfloat16, device=dev)
+    yf = torch.empty(shape + (co,), dtype=torch.float32, device=dev)
+    nn.mach_nn_conv3d_tc(x, wpk, co, b, y, yf, act=act)
+    assert nn.mach_nn_device_status() == 0
+    z = U.conv3d(xh, wh, b.cpu().double().numpy())
+    ref = U.lrelu(z) if act else z
+    bound = (27 * ci + 2) * 2.0 ** -24 * (U.conv3d(np.abs(xh), np.abs(wh)) + np.abs(b.cpu().double().numpy()))
+    got = yf.cpu().double().numpy()
+    assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) - bound)
+    gb = y.cpu().double().numpy()
+    assert np.all(np.abs(gb - ref) <= 2.0 ** -8 * (np.abs(ref) + bound) + bound)
+
+
+@pytest.mark.parametrize("ci,co,shape", CONV_CASES)
+def test_conv3d_tcgen05_flip_is_the_data_gradient(ci, co, shape):
+    nn = _nn()
+    r = np.random.default_rng(ci * 7 + co + 3)
+    gy, gyh = _bf(r.standard_normal(shape + (co,)))
+    w, wh = _bf(r.standard_normal((27, ci, co)) * 0.1)
+    _, wpkt = nn.mach_nn_pack_weights(w.float(), ci, co, forward=False)
+    gx = torch.empty(shape + (ci,), dtype=torch.float32, device=dev)
+    nn.mach_nn_conv3d_tc(gy, wpkt, ci, None, None, gx, flip=True)
+    assert nn.mach_nn_device_status() == 0
+    ref = U.conv3d_grad_input(gyh, wh)
+    bound = (27 * co + 2) * 2.0 ** -24 * U.conv3d_grad_input(np.abs(gyh), np.abs(wh))
+    assert np.all(np.abs(gx.cpu().double().numpy() - ref) <= bound)
+
+
+def test_tcgen05_and_mma_sync_agree():
+    # the two convolution kernels sum the same products in different orders
+    nn = _nn()
+    r = np.random.default_rng(8)
+    ci, co, shape = 64, 64, (2, 8, 32, 16)
+    x, _ = _bf(r.standard_normal(shape + (ci,)))
+    w, _ = _bf(r.standard_normal((27, ci, co)) * 0.05)
+    wpk, _ = nn.mach_nn_pack_weights(w.float(), ci, co, flipped=False)
+    a = torch.empty(shape + (co,), dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    nn.mach_nn_conv3d_tc(x, wpk, co, None, None, a)
+    nn.mach_nn_conv3d(x, w, None, None, b)
+    torch.cuda.synchronize()
+    assert float((a - b).abs().max()) <= 1e-4 * float(b.abs().max())
+
+
 WGRAD_CASES = [(16, 16), (16, 32), (16, 64), (32, 16), (32, 32), (32, 64), (48, 16), (96, 32), (192, 64),
                (64, 128)]
 
@@ -190,8 +262,9 @@ def _cos(a, b):
     return float((a * b).sum() / (np.linalg.norm(a) * np.linalg.norm(b)))
 
 
+@pytest.mark.parametrize("backend", ["tcgen05", "mma.sync"])
 @pytest.mark.parametrize("levels,dims,batch", [(4, (16, 8, 8), 2), (2, (6, 4, 10), 3), (1, (3, 5, 7), 1)])
-def test_network_forward_backward_matches_oracle(levels, dims, batch):
+def test_network_forward_backward_matches_oracle(levels, dims, batch, backend):
     nn = _nn()
     nz, ny, nx = dims
     V = nz * ny * nx
@@ -208,6 +281,7 @@ def test_network_forward_backward_matches_oracle(levels, dims, batch):
         net.set_params(p)
         np.testing.assert_array_equal(net.params(), p)
         net.set_gain(gain)
+        net.set_backend(backend)
         yd = torch.as_tensor(y).to(dev)
         td = torch.as_tensor(t).to(dev)
         loss = torch.zeros(1, device=dev)
