@@ -140,7 +140,7 @@ __device__ __forceinline__ TileCoord tile_coord(const ConvTcParams& p, int64_t t
   return c;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_conv3d_tc(const __grid_constant__ CUtensorMap xmap,
+__global__ void __launch_bounds__(kThreads, 3) k_conv3d_tc(const __grid_constant__ CUtensorMap xmap,
                                                            const ConvTcParams p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -475,14 +475,23 @@ cudaError_t launch_conv_tc(const void* x, const void* wpk, const float* bias, vo
   if (e != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_conv3d_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
     return e;
-  int dev = 0, sms = 0, per_sm = 0;
+  int dev = 0, sms = 0, smem_sm = 0, regs_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv3d_tc, kThreads, smem)) != cudaSuccess)
+  if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
     return e;
-  // tensor memory holds 512 columns per SM: CTAs beyond that would wait in allocation
-  const int tmem_fit = static_cast<int>(512 / p.tmem_cols);
-  per_sm = per_sm < tmem_fit ? per_sm : tmem_fit;
+  if ((e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess) return e;
+  cudaFuncAttributes fa{};
+  if ((e = cudaFuncGetAttributes(&fa, k_conv3d_tc)) != cudaSuccess) return e;
+  // resident CTAs per SM: shared memory (1 KB reserved per CTA), registers (allocated per
+  // warp in units of 256), and tensor memory (512 columns per SM; a CTA beyond that would
+  // wait in allocation)
+  const int by_smem = smem_sm / static_cast<int>(smem + 1024);
+  const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+  const int by_regs = regs_sm / (regs_warp * (kThreads / 32));
+  const int by_tmem = static_cast<int>(512 / p.tmem_cols);
+  int per_sm = by_smem < by_regs ? by_smem : by_regs;
+  per_sm = per_sm < by_tmem ? per_sm : by_tmem;
   per_sm = per_sm < 1 ? 1 : per_sm;
   const int64_t grid = p.tiles < static_cast<int64_t>(sms) * per_sm ? p.tiles : static_cast<int64_t>(sms) * per_sm;
   k_conv3d_tc<<<static_cast<unsigned>(grid), kThreads, smem, s>>>(map, p);
