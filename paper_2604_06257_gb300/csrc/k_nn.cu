@@ -10,8 +10,9 @@
 //    output conversion are fused into the epilogue.  With `flip` the taps are mirrored,
 //    which turns it into the data gradient (given the transposed weights [27][Cout][Cin]).
 //  * k_conv3d_wgrad: weight gradient dW[t][ci][co] = sum_v X[v + off(t)][ci] dY[v][co]:
-//    per block one tap and one WM x WN (ci, co) tile, voxels split across blocks, partial
-//    sums added with float32 atomics.
+//    per block all 27 taps of one (16 input, CT output channel) block over a run of voxel
+//    tiles, halo and gradient tiles staged once per tile, partial sums added with float32
+//    atomics.
 //  * elementwise kernels: leaky-ReLU backward, 2x average pooling and nearest upsampling
 //    (and their adjoints), channel-slice copies (concatenation), bias gradient, Adam,
 //    and the network boundary (RMS normalisation / packing, loss, output).
@@ -170,93 +171,120 @@ __global__ void __launch_bounds__(128) k_conv3d(const bf16* __restrict__ X, cons
   }
 }
 
-// Weight gradient.  Block = (voxel split, tap, (ci, co) tile of WM x WN); 4 warps arranged
-// as WARPS_M x WARPS_N tiles of 16 x NW, times KSPLIT slices of the voxel (K) dimension.
-template <int WM, int WN>
-__global__ void __launch_bounds__(128) k_conv3d_wgrad(const bf16* __restrict__ X, const bf16* __restrict__ dY,
-                                                      float* __restrict__ dW, int N, int D, int H, int W, int Ci,
-                                                      int Co, int64_t vox_per_split) {
-  constexpr int WARPS_M = WM / 16;
-  constexpr int NW = WN >= 32 ? 32 : 16;
-  constexpr int WARPS_N = WN / NW;
-  constexpr int KSPLIT = 4 / (WARPS_M * WARPS_N);
-  constexpr int KV = 16 * KSPLIT;   // voxels per stage
-  static_assert(WARPS_M * WARPS_N * KSPLIT == 4, "four warps");
-  __shared__ __align__(128) bf16 sX[2][KV][WM + 8];
-  __shared__ __align__(128) bf16 sG[2][KV][WN + 8];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp % WARPS_M, wn = (warp / WARPS_M) % WARPS_N, wk = warp / (WARPS_M * WARPS_N);
-  const int t = blockIdx.y;
-  const int nco = Co / WN;
-  const int ci0 = (blockIdx.z / nco) * WM, co0 = (blockIdx.z % nco) * WN;
-  const int64_t M = static_cast<int64_t>(N) * D * H * W;
-  const int64_t v_begin = static_cast<int64_t>(blockIdx.x) * vox_per_split;
-  const int64_t v_end = v_begin + vox_per_split < M ? v_begin + vox_per_split : M;
-  int dz, dy, dx;
-  tap_offset(t, dz, dy, dx);
+// Weight gradient, all 27 taps per block.  A block owns one 16-channel input block, one
+// CT-channel output block and a run of 8 x 16 x 1 voxel tiles.  Per tile it stages the
+// input halo brick (10 x 18 x 3 voxels x 16 channels, zero outside the volume) and the
+// output-gradient tile (128 voxels x CT channels, zero outside) in shared memory once,
+// and every warp accumulates its taps (warp w: taps w, w + 8, w + 16, w + 24) as
+// mma.sync products X_t^T (16 x 16 voxels) x dY (16 voxels x CT) over the tile's voxels.
+// Partial sums are added to dW with float32 atomics at the end.
+constexpr int kWTaps = 4;              // taps per warp (8 warps cover 27)
+constexpr int kHRows = 10 * 18 * 3;    // halo rows of one 8-channel group
 
-  auto load = [&](int stage, int64_t v0) {
-    constexpr int XCH = KV * WM / 8, GCH = KV * WN / 8;
-    for (int c = tid; c < XCH + GCH; c += 128) {
-      if (c < XCH) {
-        const int r = c / (WM / 8), cc = c % (WM / 8);
-        const int64_t v = v0 + r;
-        const bf16* src = X;
-        bool ok = v < v_end;
-        if (ok) {
-          const Vox p = vox_of(v, D, H, W);
-          const int z = p.z + dz, y = p.y + dy, x = p.x + dx;
-          ok = z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W;
-          if (ok) src = X + ((((static_cast<int64_t>(p.n) * D + z) * H + y) * W + x) * Ci + ci0 + cc * 8);
-        }
-        cp16(&sX[stage][r][cc * 8], src, ok ? 16 : 0);
+template <int CT>
+__global__ void __launch_bounds__(256) k_conv3d_wgrad(const bf16* __restrict__ X, const bf16* __restrict__ dY,
+                                                      float* __restrict__ dW, int N, int D, int H, int W, int Ci,
+                                                      int Co, int64_t tiles, int tiles_x, int tiles_y,
+                                                      int64_t tiles_per_block) {
+  constexpr int kHaloB = 2 * kHRows * 16;
+  constexpr int kGB = (CT / 8) * 128 * 16;
+  constexpr int kStage = kHaloB + kGB;
+  extern __shared__ __align__(128) uint8_t wsm[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int cb = blockIdx.y, ob = blockIdx.z;
+  const int64_t t_begin = static_cast<int64_t>(blockIdx.x) * tiles_per_block;
+  const int64_t t_end = t_begin + tiles_per_block < tiles ? t_begin + tiles_per_block : tiles;
+
+  auto load = [&](int stage, int64_t tile) {
+    const int tx = static_cast<int>(tile % tiles_x);
+    int64_t r0 = tile / tiles_x;
+    const int ty = static_cast<int>(r0 % tiles_y);
+    r0 /= tiles_y;
+    const int z = static_cast<int>(r0 % D), n = static_cast<int>(r0 / D);
+    const int x0 = tx * 8, y0 = ty * 16;
+    uint8_t* base = wsm + stage * kStage;
+    for (int c = tid; c < 2 * kHRows + (CT / 8) * 128; c += 256) {
+      if (c < 2 * kHRows) {
+        const int g = c / kHRows, r = c % kHRows;
+        const int hz = r / 180, hr = r % 180, hy = hr / 10, hx = hr % 10;
+        const int x = x0 - 1 + hx, y = y0 - 1 + hy, zz = z - 1 + hz;
+        const bool in = x >= 0 && x < W && y >= 0 && y < H && zz >= 0 && zz < D;
+        const bf16* src = in ? X + ((((static_cast<int64_t>(n) * D + zz) * H + y) * W + x) * Ci + cb * 16 + g * 8) : X;
+        cp16(base + (g * kHRows + r) * 16, src, in ? 16 : 0);
       } else {
-        const int c2 = c - XCH;
-        const int r = c2 / (WN / 8), cc = c2 % (WN / 8);
-        const int64_t v = v0 + r;
-        const bool ok = v < v_end;
-        cp16(&sG[stage][r][cc * 8], ok ? dY + v * Co + co0 + cc * 8 : dY, ok ? 16 : 0);
+        const int c2 = c - 2 * kHRows;
+        const int cg = c2 / 128, k = c2 % 128;
+        const int x = x0 + (k & 7), y = y0 + (k >> 3);
+        const bool in = x < W && y < H;
+        const bf16* src = in ? dY + ((((static_cast<int64_t>(n) * D + z) * H + y) * W + x) * Co + ob * CT + cg * 8) : dY;
+        cp16(base + kHaloB + (cg * 128 + k) * 16, src, in ? 16 : 0);
       }
     }
     cp_commit();
   };
 
-  float acc[NW / 8][4];
+  float acc[kWTaps][CT / 8][4];
 #pragma unroll
-  for (int j = 0; j < NW / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-  const int64_t steps = v_end > v_begin ? (v_end - v_begin + KV - 1) / KV : 0;
-  if (steps > 0) load(0, v_begin);
-  for (int64_t s = 0; s < steps; ++s) {
-    const int st = static_cast<int>(s & 1);
-    if (s + 1 < steps) {
-      load(st ^ 1, v_begin + (s + 1) * KV);
+  for (int i = 0; i < kWTaps; ++i)
+#pragma unroll
+    for (int j = 0; j < CT / 8; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
+
+  if (t_begin < t_end) load(0, t_begin);
+  for (int64_t tile = t_begin; tile < t_end; ++tile) {
+    const int st = static_cast<int>((tile - t_begin) & 1);
+    if (tile + 1 < t_end) {
+      load(st ^ 1, tile + 1);
       cp_wait<1>();
     } else {
       cp_wait<0>();
     }
     __syncthreads();
-    // A (m = input channel, k = voxel) is sX transposed: transposing ldmatrix
-    uint32_t af[4];
-    ldm_x4_t(af, &sX[st][wk * 16 + (lane & 7) + ((lane >> 4) << 3)][wm * 16 + ((lane >> 3) & 1) * 8]);
+    const uint8_t* base = wsm + st * kStage;
+    const uint8_t* halo = base;
+    const uint8_t* gt = base + kHaloB;
+#pragma unroll 2
+    for (int ks = 0; ks < 8; ++ks) {   // 16 voxels (two x-rows of the tile) per K step
+      uint32_t bfr[CT / 16][4];
 #pragma unroll
-    for (int j = 0; j < NW / 16; ++j) {
-      uint32_t bfr[4];
-      ldm_x4_t(bfr, &sG[st][wk * 16 + (lane & 15)][wn * NW + j * 16 + (lane >> 4) * 8]);
-      mma_bf16(acc[2 * j], af, bfr[0], bfr[1]);
-      mma_bf16(acc[2 * j + 1], af, bfr[2], bfr[3]);
+      for (int j = 0; j < CT / 16; ++j)
+        ldm_x4_t(bfr[j], gt + ((2 * j + (lane >> 4)) * 128 + ks * 16 + (lane & 15)) * 16);
+      const int mat = lane >> 3;
+      const int kv = ks * 16 + (mat >> 1) * 8 + (lane & 7);   // voxel of this lane's row address
+      const int mx = kv & 7, my = kv >> 3;
+#pragma unroll
+      for (int i = 0; i < kWTaps; ++i) {
+        const int t = warp + 8 * i;
+        if (t < 27) {   // warp-uniform
+          int dz, dy, dx;
+          tap_offset(t, dz, dy, dx);
+          const int row = (dz + 1) * 180 + (my + dy + 1) * 10 + (mx + dx + 1);
+          uint32_t af[4];
+          ldm_x4_t(af, halo + ((mat & 1) * kHRows + row) * 16);
+#pragma unroll
+          for (int j = 0; j < CT / 16; ++j) {
+            mma_bf16(acc[i][2 * j], af, bfr[j][0], bfr[j][1]);
+            mma_bf16(acc[i][2 * j + 1], af, bfr[j][2], bfr[j][3]);
+          }
+        }
+      }
     }
     __syncthreads();
   }
-  if (steps == 0) return;
+  if (t_begin >= t_end) return;
 #pragma unroll
-  for (int j = 0; j < NW / 8; ++j) {
-    const int co = co0 + wn * NW + 8 * j + 2 * (lane & 3);
+  for (int i = 0; i < kWTaps; ++i) {
+    const int t = warp + 8 * i;
+    if (t >= 27) continue;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int ci = ci0 + wm * 16 + (lane >> 2) + 8 * h;
-      float* dst = dW + (static_cast<int64_t>(t) * Ci + ci) * Co + co;
-      atomicAdd(dst, acc[j][2 * h]);
-      atomicAdd(dst + 1, acc[j][2 * h + 1]);
+    for (int j = 0; j < CT / 8; ++j) {
+      const int co = ob * CT + 8 * j + 2 * (lane & 3);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int ci = cb * 16 + (lane >> 2) + 8 * h;
+        float* dst = dW + (static_cast<int64_t>(t) * Ci + ci) * Co + co;
+        atomicAdd(dst, acc[i][j][2 * h]);
+        atomicAdd(dst + 1, acc[i][j][2 * h + 1]);
+      }
     }
   }
 }
@@ -266,6 +294,25 @@ __global__ void k_lrelu_bwd(bf16* __restrict__ g, const bf16* __restrict__ y, in
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (!(__bfloat162float(y[i]) > 0.f)) g[i] = __float2bfloat16_rn(__bfloat162float(g[i]) * kLeak);
+}
+
+// the same, 8 elements (16 bytes) per thread
+__global__ void k_lrelu_bwd8(uint4* __restrict__ g, const uint4* __restrict__ y, int64_t n8) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n8) return;
+  uint4 gv = g[i];
+  const uint4 yv = y[i];
+  uint32_t* gw = reinterpret_cast<uint32_t*>(&gv);
+  const uint32_t* yw = reinterpret_cast<const uint32_t*>(&yv);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    __nv_bfloat162 g2 = *reinterpret_cast<const __nv_bfloat162*>(&gw[k]);
+    const __nv_bfloat162 y2 = *reinterpret_cast<const __nv_bfloat162*>(&yw[k]);
+    const float2 gf = __bfloat1622float2(g2), yf = __bfloat1622float2(y2);
+    g2 = __floats2bfloat162_rn(yf.x > 0.f ? gf.x : gf.x * kLeak, yf.y > 0.f ? gf.y : gf.y * kLeak);
+    gw[k] = *reinterpret_cast<const uint32_t*>(&g2);
+  }
+  g[i] = gv;
 }
 
 // 2x average pooling [N][D][H][W][C] -> [N][D/2][H/2][W/2][C]
@@ -512,19 +559,23 @@ inline unsigned nblocks(int64_t n, int b = 256) { return static_cast<unsigned>((
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 inline mach_status last_status() { return cudaGetLastError() == cudaSuccess ? MACH_OK : MACH_ERR_CUDA; }
 
-template <int WM, int WN>
-void go_wgrad(const bf16* x, const bf16* dy, float* dw, int n, int d, int h, int w, int ci, int co, cudaStream_t s) {
-  constexpr int NW = WN >= 32 ? 32 : 16;
-  constexpr int KV = 16 * (4 / ((WM / 16) * (WN / NW)));
-  const int64_t M = static_cast<int64_t>(n) * d * h * w;
-  const int64_t tiles = 27LL * (ci / WM) * (co / WN);
-  // enough voxel splits for about 8 blocks per SM, each at least 512 voxels
-  int64_t splits = (152LL * 8 + tiles - 1) / tiles;
-  int64_t per = (M + splits - 1) / splits;
-  per = per < 512 ? 512 : (per + KV - 1) / KV * KV;
-  splits = (M + per - 1) / per;
-  const dim3 grid(static_cast<unsigned>(splits), 27, static_cast<unsigned>((ci / WM) * (co / WN)));
-  k_conv3d_wgrad<WM, WN><<<grid, 128, 0, s>>>(x, dy, dw, n, d, h, w, ci, co, per);
+template <int CT>
+cudaError_t go_wgrad(const bf16* x, const bf16* dy, float* dw, int n, int d, int h, int w, int ci, int co,
+                     cudaStream_t s) {
+  const int tiles_x = (w + 7) / 8, tiles_y = (h + 15) / 16;
+  const int64_t tiles = static_cast<int64_t>(tiles_x) * tiles_y * d * n;
+  const int64_t chan_blocks = static_cast<int64_t>(ci / 16) * (co / CT);
+  // about four blocks per SM in total, split over runs of tiles
+  int64_t splits = (152LL * 4 + chan_blocks - 1) / chan_blocks;
+  splits = splits < tiles ? splits : tiles;
+  const int64_t per = (tiles + splits - 1) / splits;
+  splits = (tiles + per - 1) / per;
+  const int smem = 2 * (2 * kHRows * 16 + (CT / 8) * 128 * 16);
+  cudaError_t e = cudaFuncSetAttribute(k_conv3d_wgrad<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid(static_cast<unsigned>(splits), static_cast<unsigned>(ci / 16), static_cast<unsigned>(co / CT));
+  k_conv3d_wgrad<CT><<<grid, 256, smem, s>>>(x, dy, dw, n, d, h, w, ci, co, tiles, tiles_x, tiles_y, per);
+  return cudaGetLastError();
 }
 }  // namespace
 
@@ -561,15 +612,10 @@ mach_status mach_nn_conv3d_wgrad(const void* x, const void* dy, float* dw, int32
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bf16* X = static_cast<const bf16*>(x);
   const bf16* G = static_cast<const bf16*>(dy);
-  const bool m32 = ci % 32 == 0;
-  const int wn = co % 64 == 0 ? 64 : (co % 32 == 0 ? 32 : 16);
-  if (m32 && wn == 64) go_wgrad<32, 64>(X, G, dw, n, nz, ny, nx, ci, co, s);
-  else if (m32 && wn == 32) go_wgrad<32, 32>(X, G, dw, n, nz, ny, nx, ci, co, s);
-  else if (m32) go_wgrad<32, 16>(X, G, dw, n, nz, ny, nx, ci, co, s);
-  else if (wn == 64) go_wgrad<16, 64>(X, G, dw, n, nz, ny, nx, ci, co, s);
-  else if (wn == 32) go_wgrad<16, 32>(X, G, dw, n, nz, ny, nx, ci, co, s);
-  else go_wgrad<16, 16>(X, G, dw, n, nz, ny, nx, ci, co, s);
-  return last_status();
+  if (ci / 16 > 65535 || co / 16 > 65535) return MACH_ERR_UNSUPPORTED;
+  const cudaError_t e = co % 32 == 0 ? go_wgrad<32>(X, G, dw, n, nz, ny, nx, ci, co, s)
+                                     : go_wgrad<16>(X, G, dw, n, nz, ny, nx, ci, co, s);
+  return e == cudaSuccess ? MACH_OK : MACH_ERR_CUDA;
 }
 
 mach_status mach_nn_bias_grad(const void* g, float* db, int64_t voxels, int32_t c, void* stream) {
@@ -585,8 +631,12 @@ mach_status mach_nn_bias_grad(const void* g, float* db, int64_t voxels, int32_t 
 mach_status mach_nn_lrelu_bwd(void* g, const void* y, int64_t count, void* stream) {
   if (!g || !y || count < 0) return MACH_ERR_INVALID_ARG;
   if (count == 0) return MACH_OK;
-  k_lrelu_bwd<<<nblocks(count), 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<bf16*>(g),
-                                                                               static_cast<const bf16*>(y), count);
+  if (count % 8 == 0 && aligned16(g) && aligned16(y))
+    k_lrelu_bwd8<<<nblocks(count / 8), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<uint4*>(g), static_cast<const uint4*>(y), count / 8);
+  else
+    k_lrelu_bwd<<<nblocks(count), 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<bf16*>(g),
+                                                                                 static_cast<const bf16*>(y), count);
   return last_status();
 }
 

@@ -222,6 +222,10 @@ def test_lrelu_backward_and_bias_gradient():
     y, yh = _bf(r.standard_normal((3, 5, 7, 9, 32)))
     nn.mach_nn_lrelu_bwd(g, y)
     np.testing.assert_array_equal(g.cpu().double().numpy(), np.where(yh > 0, gh, gh / 64.0))
+    g1, g1h = _bf(r.standard_normal(37))          # a count the 16-byte path cannot take
+    y1, y1h = _bf(r.standard_normal(37))
+    nn.mach_nn_lrelu_bwd(g1, y1)
+    np.testing.assert_array_equal(g1.cpu().double().numpy(), np.where(y1h > 0, g1h, g1h / 64.0))
     for c in (16, 32, 64, 128):
         gg, ggh = _bf(r.standard_normal((2, 5, 7, 9, c)))
         db = torch.zeros(c, dtype=torch.float32, device=dev)
