@@ -143,6 +143,22 @@ mach_status mach_iq_convert(const void *src_dev, int32_t src_order, void *dst_de
                             int32_t n_tx, int32_t n_elem, int32_t n_samples, int32_t n_frames,
                             void *stream);
 
+/* RF input (Sec. 3: the method takes RF or IQ channel data): demodulate real RF samples
+ * into the complex IQ that mach_das_run reads.
+ *   rf_dev  float32 [n_tx][n_elem][n_rf][n_frames] (device), sample m at t0 + m / fs_rf;
+ *   iq_dev  complex64 [n_tx][n_elem][n_iq][n_frames] (device), n_iq = (n_rf - 1) / decim + 1,
+ *           sample n at t0 + n decim / fs_rf (so the plan's fs = fs_rf / decim, same t0);
+ *   iq[n] = sum_{k<L} taps[k] rf[n decim + k - (L-1)/2] exp(-j 2 pi fc (t0 + (n decim + k - (L-1)/2) / fs_rf)),
+ *           RF samples outside [0, n_rf) read as zero.
+ * taps: host float [n_taps] low-pass filter (1 <= n_taps <= 128), copied.  For an echo
+ * A g(t - tau) cos(2 pi fc (t - tau)) and a filter of unit DC gain that passes g's band and
+ * stops 2 fc, iq approximates (A / 2) g(t - tau) exp(-j 2 pi fc tau), the IQ model of the
+ * plan.  Arguments are checked before the launch; MACH_ERR_INVALID_ARG for bad sizes,
+ * rates, taps or alignment. */
+mach_status mach_rf_to_iq(const float *rf_dev, void *iq_dev, int32_t n_tx, int32_t n_elem, int32_t n_rf,
+                          int32_t n_frames, double fs_rf, double fc, double t0, const float *taps,
+                          int32_t n_taps, int32_t decim, void *stream);
+
 /* Release a plan and its device tables (synchronises the device).  NULL is a no-op. */
 /* Uncompounded output (the output shape of the paper's memory table, Table 3: voxels x
  * compounded planes x frames): y_dev complex64 [n_vox][n_tx][n_frames], element

@@ -32,7 +32,8 @@ EXPORTS = ("mach_das_plan", "mach_das_run", "mach_power_doppler", "mach_plan_des
            "mach_version", "mach_debug_fail_alloc_after", "mach_plan_device_status",
            "mach_debug_force_variant", "mach_debug_set_wait_limit", "mach_debug_stall_producer",
            "mach_das_run_noalloc", "mach_iq_convert", "mach_batch_plan", "mach_batch_bind",
-           "mach_batch_run", "mach_batch_get_info", "mach_batch_destroy", "mach_das_run_per_tx")
+           "mach_batch_run", "mach_batch_get_info", "mach_batch_destroy", "mach_das_run_per_tx",
+           "mach_rf_to_iq")
 
 
 class MachError(RuntimeError):
@@ -95,6 +96,9 @@ def lib():
         L.mach_das_plan.argtypes = [C.POINTER(mach_das_desc), vp, C.POINTER(vp)]
         L.mach_das_run.argtypes = [vp, vp, vp, vp]
         L.mach_das_run_per_tx.argtypes = [vp, vp, vp, vp]
+        L.mach_rf_to_iq.argtypes = [vp, vp, i32, i32, i32, i32, C.c_double, C.c_double, C.c_double, vp, i32,
+                                    i32, vp]
+        L.mach_rf_to_iq.restype = C.c_int
         L.mach_das_run_per_tx.restype = C.c_int
         L.mach_power_doppler.argtypes = [vp, vp, vp, vp, vp]
         L.mach_plan_destroy.argtypes = [vp]
@@ -289,6 +293,23 @@ def mach_iq_convert(src, src_order, dst, dst_dtype, n_tx, n_elem, n_samples, n_f
                                int(n_frames), _stream_ptr(stream))
     if st != MACH_OK:
         raise MachError(st, "mach_iq_convert")
+
+
+def mach_rf_to_iq(rf, taps, fs_rf: float, fc: float, t0: float = 0.0, decim: int = 1, iq=None, stream=None):
+    """Demodulate real RF [T, C, S_rf, F] (float32 CUDA tensor) into complex64 IQ
+    [T, C, (S_rf - 1) // decim + 1, F] (mach.h: mach_rf_to_iq)."""
+    import torch
+    T, Cn, S, F = rf.shape
+    n_iq = (S - 1) // decim + 1
+    if iq is None:
+        iq = torch.empty((T, Cn, n_iq, F), dtype=torch.complex64, device=rf.device)
+    h = np.ascontiguousarray(taps, dtype=np.float32)
+    st = lib().mach_rf_to_iq(_dev_ptr(rf, "rf", torch.float32), _dev_ptr(iq, "iq", torch.complex64, T * Cn * n_iq * F),
+                             T, Cn, S, F, float(fs_rf), float(fc), float(t0), h.ctypes.data, len(h), int(decim),
+                             _stream_ptr(stream))
+    if st != MACH_OK:
+        raise MachError(st, "mach_rf_to_iq")
+    return iq
 
 
 def prepare_iq(src, src_order="ftcs", dtype="c64", shape=None, stream=None):

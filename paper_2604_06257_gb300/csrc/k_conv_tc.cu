@@ -140,6 +140,7 @@ __device__ __forceinline__ TileCoord tile_coord(const ConvTcParams& p, int64_t t
   return c;
 }
 
+template <bool FLIP, int TZ>
 __global__ void __launch_bounds__(kThreads, 3) k_conv3d_tc(const __grid_constant__ CUtensorMap xmap,
                                                            const ConvTcParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -233,7 +234,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_conv3d_tc(const __grid_constant
   } else if (warp == 1) {
     if (lane == 0) {   // ---------------------------------------------- MMAs
       const uint32_t idesc = instr_desc(p.Co);
-      const uint32_t plane = static_cast<uint32_t>(kHX * kHY);
       bool ok = !p.resident || wait_spin(&fullB[0], 0, limit);
       if (!ok) give_up();
       uint32_t a_use = 0, b_use = 0, acc_use = 0;
@@ -252,12 +252,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_conv3d_tc(const __grid_constant
             ok = false;
             break;
           }
-          const uint32_t a_base = smem_u32(sA + sa * a_stage);
-          for (int t0 = 0; t0 < 27 && ok; t0 += 9) {
+          // descriptors: the taps differ only by start address (16-byte units in the low
+          // field), so every MMA costs two additions; the 27 taps unroll at compile time
+          const uint64_t ad0 = smem_desc(smem_u32(sA + sa * a_stage), p.group_pitch, kHX * 16);
+#pragma unroll
+          for (int tb = 0; tb < 3; ++tb) {
             uint32_t w_base;
             uint32_t sb = 0;
             if (p.resident) {
-              w_base = smem_u32(sW) + (static_cast<uint32_t>(kc) * 27 + t0) * tap_bytes;
+              w_base = smem_u32(sW) + (static_cast<uint32_t>(kc) * 27 + tb * 9) * tap_bytes;
             } else {
               sb = b_use % kNB;
               if (!wait_spin(&fullB[sb], (b_use / kNB) & 1u, limit)) {
@@ -267,20 +270,19 @@ __global__ void __launch_bounds__(kThreads, 3) k_conv3d_tc(const __grid_constant
               }
               w_base = smem_u32(sW + sb * 9 * tap_bytes);
             }
-            for (int t = t0; t < t0 + 9; ++t) {
-              int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-              if (p.flip) {
-                dz = -dz;
-                dy = -dy;
-                dx = -dx;
-              }
-              const uint64_t bd = smem_desc(w_base + static_cast<uint32_t>(t - t0) * tap_bytes,
-                                            static_cast<uint32_t>(p.Co) * 16u, 128u);
-              for (int zz = 0; zz < p.tz; ++zz) {
-                const uint32_t row = static_cast<uint32_t>((zz + dz + 1) * plane + (dy + 1) * kHX + (dx + 1));
-                const uint64_t ad = smem_desc(a_base + row * 16u, p.group_pitch, kHX * 16);
-                mma_f16(d0 + static_cast<uint32_t>(zz * p.Co), ad, bd, idesc, (kc > 0 || t > 0) ? 1u : 0u);
-              }
+            const uint64_t bd0 = smem_desc(w_base, static_cast<uint32_t>(p.Co) * 16u, 128u);
+#pragma unroll
+            for (int tt = 0; tt < 9; ++tt) {
+              const int t = tb * 9 + tt;
+              const int sg = FLIP ? -1 : 1;
+              const int dz = sg * (t / 9 - 1), dy = sg * ((t / 3) % 3 - 1), dx = sg * (t % 3 - 1);
+              const uint32_t row = static_cast<uint32_t>((dz + 1) * (kHX * kHY) + (dy + 1) * kHX + (dx + 1));
+              const uint64_t bd = bd0 + static_cast<uint64_t>(tt) * (tap_bytes >> 4);
+              const uint32_t acc = (kc > 0 || t > 0) ? 1u : 0u;
+#pragma unroll
+              for (int zz = 0; zz < TZ; ++zz)
+                mma_f16(d0 + static_cast<uint32_t>(zz * p.Co), ad0 + row + static_cast<uint32_t>(zz * kHX * kHY),
+                        bd, idesc, acc);
             }
             if (!p.resident) {
               mma_commit(&emptyB[sb]);
@@ -313,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_conv3d_tc(const __grid_constant
       __syncwarp();
       fence_after();
       const int x = tc.x0 + mx, y = tc.y0 + my;
-      for (int zz = 0; zz < p.tz; ++zz) {
+      for (int zz = 0; zz < TZ; ++zz) {
         const int z = tc.z0 + zz;
         const bool inside = x < p.W && y < p.H && z < p.D;
         const int64_t v = ((static_cast<int64_t>(tc.n) * p.D + z) * p.H + y) * p.W + x;
@@ -471,9 +473,11 @@ cudaError_t launch_conv_tc(const void* x, const void* wpk, const float* bias, vo
   p.tmem_cols = shp.tmem_cols;
   p.wait_limit = kDefaultWait;
   const size_t smem = shp.smem;
-  cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  auto kern = flip ? (shp.tz == 2 ? k_conv3d_tc<true, 2> : k_conv3d_tc<true, 1>)
+                  : (shp.tz == 2 ? k_conv3d_tc<false, 2> : k_conv3d_tc<false, 1>);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_conv3d_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
     return e;
   int dev = 0, sms = 0, smem_sm = 0, regs_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -482,7 +486,7 @@ cudaError_t launch_conv_tc(const void* x, const void* wpk, const float* bias, vo
     return e;
   if ((e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess) return e;
   cudaFuncAttributes fa{};
-  if ((e = cudaFuncGetAttributes(&fa, k_conv3d_tc)) != cudaSuccess) return e;
+  if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
   // resident CTAs per SM: shared memory (1 KB reserved per CTA), registers (allocated per
   // warp in units of 256), and tensor memory (512 columns per SM; a CTA beyond that would
   // wait in allocation)
@@ -494,7 +498,7 @@ cudaError_t launch_conv_tc(const void* x, const void* wpk, const float* bias, vo
   per_sm = per_sm < by_tmem ? per_sm : by_tmem;
   per_sm = per_sm < 1 ? 1 : per_sm;
   const int64_t grid = p.tiles < static_cast<int64_t>(sms) * per_sm ? p.tiles : static_cast<int64_t>(sms) * per_sm;
-  k_conv3d_tc<<<static_cast<unsigned>(grid), kThreads, smem, s>>>(map, p);
+  kern<<<static_cast<unsigned>(grid), kThreads, smem, s>>>(map, p);
   return cudaGetLastError();
 }
 

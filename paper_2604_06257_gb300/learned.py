@@ -111,8 +111,14 @@ def scene_weights(rng: np.random.Generator, M: int, count: int, k=(6, 16)) -> np
 
 
 def compose(bank: Bank, W):
-    """(few, many) complex64 [V, B] volumes of the scenes with block weights W [M, B]."""
-    return bank.few @ W, bank.many @ W
+    """(few, many) complex64 [V, B] volumes of the scenes with block weights W [M, B]
+    (only the blocks some scene uses are read)."""
+    used = (W != 0).any(dim=1).nonzero().flatten()
+    if len(used) == 0:
+        z = bank.few.new_zeros((bank.few.shape[0], W.shape[1]))
+        return z, z.clone()
+    Wu = W.index_select(0, used)
+    return bank.few.index_select(1, used) @ Wu, bank.many.index_select(1, used) @ Wu
 
 
 def flip(vol, n: int, fx: bool, fy: bool):
@@ -218,11 +224,11 @@ def load(path: str):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--n", type=int, default=128)
-    ap.add_argument("--bank", type=int, default=512)
-    ap.add_argument("--samples", type=int, default=2000)
-    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--bank", type=int, default=1024)
+    ap.add_argument("--samples", type=int, default=4000)
+    ap.add_argument("--epochs", type=int, default=6)
     ap.add_argument("--batch", type=int, default=8)
-    ap.add_argument("--lr", type=float, default=5e-4)
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default=os.path.join(WEIGHTS_DIR, "unet_few3_many21_128.npz"))
     ap.add_argument("--report", default=None)

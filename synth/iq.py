@@ -154,3 +154,43 @@ def simulate_frames(acq: Acquisition, phantoms, device="cpu", chunk_elems: int =
         add_echoes(buf, acq, ph.static_pos, ph.static_amp, chunk_elems=chunk_elems)
         out[..., f] = buf
     return out
+
+
+def lowpass_taps(n_taps: int, cutoff: float, fs: float) -> np.ndarray:
+    """Hann-windowed sinc low-pass (cutoff in Hz at sampling rate fs), unit DC gain."""
+    k = np.arange(n_taps) - (n_taps - 1) / 2.0
+    h = np.sinc(2.0 * cutoff / fs * k) * np.hanning(n_taps + 2)[1:-1]
+    return (h / h.sum()).astype(np.float32)
+
+
+def simulate_rf(acq: Acquisition, phantom: Phantom, decim: int, device="cpu") -> torch.Tensor:
+    """Real RF [T, C, S_rf, F] float32 of the static scatterers of ``phantom``, sampled at
+    fs_rf = decim * acq.fs from acq.t0 with S_rf = decim * (S - 1) + 1 samples, so that
+    demodulating and decimating by ``decim`` lands on the acquisition's IQ sample times.
+    Echo of a scatterer of amplitude A with round-trip time tau:
+    A g(t - tau) cos(2 pi fc (t - tau)), g the Gaussian envelope of the IQ model; every frame
+    holds the same echoes."""
+    T, C, S, F = acq.iq_shape
+    dev = torch.device(device)
+    fs_rf = decim * acq.fs
+    S_rf = decim * (S - 1) + 1
+    u = torch.as_tensor(plane_wave_directions(acq), dtype=torch.float64, device=dev)
+    el = torch.as_tensor(acq.elem_pos.astype(np.float64), dtype=torch.float64, device=dev)
+    sig = pulse_sigma_samples(acq) * decim                   # envelope sigma in RF samples
+    K = int(math.ceil(4.0 * sig))
+    offs = torch.arange(-K + 1, K + 1, device=dev, dtype=torch.int64)
+    out = torch.zeros((T, C, S_rf), dtype=torch.float64, device=dev)
+    flat = out.view(-1)
+    base = (torch.arange(T, device=dev)[:, None] * C + torch.arange(C, device=dev)[None, :]) * S_rf
+    pos = torch.as_tensor(phantom.static_pos, dtype=torch.float64, device=dev)
+    amp = torch.as_tensor(phantom.static_amp, dtype=torch.float64, device=dev)
+    for j in range(len(pos)):
+        tau = (u @ pos[j])[:, None] / acq.c + torch.linalg.norm(pos[j][None, :] - el, dim=1)[None, :] / acq.c  # [T, C]
+        s = (tau - acq.t0) * fs_rf
+        n = torch.floor(s).to(torch.int64)[..., None] + offs
+        tn = acq.t0 + n.to(torch.float64) / fs_rf
+        v = amp[j] * torch.exp(-((n.to(torch.float64) - s[..., None]) ** 2) / (2 * sig * sig)) * \
+            torch.cos(2 * math.pi * acq.fc * (tn - tau[..., None]))
+        ok = (n >= 0) & (n < S_rf)
+        flat.index_add_(0, (base[..., None] + n)[ok], v[ok])
+    return out.to(torch.float32)[..., None].expand(T, C, S_rf, F).contiguous()

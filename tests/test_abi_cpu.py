@@ -142,3 +142,21 @@ def test_network_entry_points_reject_bad_arguments_before_cuda():
                     ((4, 48, 1, 8, 8, 8), m.MACH_ERR_UNSUPPORTED)]:     # 384 channels at the bottom
         assert L.mach_unet_create(C.byref(nn.mach_unet_desc(*d)), 0, C.byref(h)) == want, d
         assert not h.value
+
+
+def test_rf_to_iq_rejects_bad_arguments_before_cuda():
+    L = m.lib()
+    fake = C.c_void_p(256)
+    h = np.ones(4, dtype=np.float32)
+    hp = h.ctypes.data
+    ok = dict(rf=fake, iq=fake, T=1, C=2, S=100, F=1, fs=20e6, fc=5e6, t0=0.0, taps=hp, L=4, D=1)
+    cases = [dict(L=0), dict(L=129), dict(D=0), dict(D=101), dict(fs=0.0), dict(fs=float("nan")),
+             dict(fc=-1.0), dict(t0=float("inf")), dict(S=0), dict(iq=None), dict(rf=C.c_void_p(258))]
+    for over in cases:
+        a = {**ok, **over}
+        st = L.mach_rf_to_iq(a["rf"], a["iq"], a["T"], a["C"], a["S"], a["F"], a["fs"], a["fc"], a["t0"],
+                             a["taps"], a["L"], a["D"], None)
+        assert st == m.MACH_ERR_INVALID_ARG, over
+    bad = np.array([1.0, np.nan], dtype=np.float32)
+    assert L.mach_rf_to_iq(fake, fake, 1, 1, 10, 1, 20e6, 5e6, 0.0, bad.ctypes.data, 2, 1, None) == \
+        m.MACH_ERR_INVALID_ARG

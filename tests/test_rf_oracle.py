@@ -1,0 +1,48 @@
+"""Pins for the RF demodulation oracle (CPU): identity filter, a pure tone, decimation,
+and the analytic echo, whose demodulated RF must be the IQ model (A/2) g e^{-j 2 pi fc tau}."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from synth import iq as iqm
+from synth import phantoms
+from oracle import rf_oracle
+
+
+def test_identity_filter_is_mixing_only():
+    r = np.random.default_rng(0)
+    rf = r.standard_normal((2, 3, 50, 4))
+    fs, fc, t0 = 40e6, 5e6, 1.3e-6
+    out = rf_oracle.rf_to_iq(rf, [1.0], fs, fc, t0, 1)
+    m = np.arange(50)
+    np.testing.assert_allclose(out, rf * np.exp(-2j * np.pi * fc * (t0 + m / fs))[None, None, :, None], rtol=1e-14)
+
+
+def test_pure_tone_demodulates_to_its_phasor():
+    fs, fc, t0, phi = 40e6, 5e6, 0.7e-6, 0.9
+    m = np.arange(400)
+    rf = np.cos(2 * np.pi * fc * (t0 + m / fs) + phi)[None, None, :, None]
+    h = iqm.lowpass_taps(65, fc, fs)
+    out = rf_oracle.rf_to_iq(rf, h, fs, fc, t0, 1)[0, 0, 40:-40, 0]
+    assert np.max(np.abs(out - 0.5 * np.exp(1j * phi) * float(np.sum(h.astype(np.float64))))) < 2e-3
+
+
+def test_decimation_subsamples():
+    r = np.random.default_rng(1)
+    rf = r.standard_normal((1, 2, 97, 3))
+    h = r.standard_normal(9)
+    full = rf_oracle.rf_to_iq(rf, h, 20e6, 3e6, 0.0, 1)
+    for d in (2, 3, 5):
+        np.testing.assert_array_equal(rf_oracle.rf_to_iq(rf, h, 20e6, 3e6, 0.0, d), full[:, :, ::d, :])
+
+
+def test_analytic_echo_demodulates_to_the_iq_model():
+    acq = synth.make_acquisition("bmode2d", "small").replace(n_frames=1)
+    ph = phantoms.Phantom(np.array([[0.5e-3, 0.0, 20e-3]]), np.array([1.0]))
+    rf = iqm.simulate_rf(acq, ph, 2)
+    h = iqm.lowpass_taps(65, acq.fc, 2 * acq.fs)
+    d = rf_oracle.rf_to_iq(rf.numpy(), h, 2 * acq.fs, acq.fc, acq.t0, 2)
+    ref = iqm.simulate(acq, ph, seed=0, snr_db=None, accum=torch.complex128).numpy()
+    err_db = 20 * np.log10(np.linalg.norm(d - ref) / np.linalg.norm(ref))
+    assert err_db < -60.0, err_db
