@@ -375,6 +375,95 @@ __global__ void k_up2_bwd(const bf16* __restrict__ dy, bf16* __restrict__ dx, in
   dx[i] = __float2bfloat16_rn(s);
 }
 
+// 16-byte (8-channel) versions of the data-movement kernels, used when every channel
+// count and offset is a multiple of 8 (always the case for the network's tensors).
+__device__ __forceinline__ void add8(float (&a)[8], uint4 v) {
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 f = __bfloat1622float2(h[k]);
+    a[2 * k] += f.x;
+    a[2 * k + 1] += f.y;
+  }
+}
+__device__ __forceinline__ uint4 pack8(const float (&a)[8], float scale) {
+  uint4 v;
+  uint32_t* w = reinterpret_cast<uint32_t*>(&v);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const __nv_bfloat162 b = __floats2bfloat162_rn(a[2 * k] * scale, a[2 * k + 1] * scale);
+    w[k] = *reinterpret_cast<const uint32_t*>(&b);
+  }
+  return v;
+}
+
+__global__ void k_pool2_v(const uint4* __restrict__ x, uint4* __restrict__ y, int N, int D, int H, int W, int C8) {
+  const int d = D / 2, h = H / 2, w = W / 2;
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= static_cast<int64_t>(N) * d * h * w * C8) return;
+  const int c = static_cast<int>(i % C8);
+  const Vox p = vox_of(i / C8, d, h, w);
+  float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int k = 0; k < 8; ++k) {
+    const int z = 2 * p.z + (k >> 2), yy = 2 * p.y + ((k >> 1) & 1), xx = 2 * p.x + (k & 1);
+    add8(a, x[((((static_cast<int64_t>(p.n) * D + z) * H + yy) * W + xx) * C8) + c]);
+  }
+  y[i] = pack8(a, 0.125f);
+}
+
+__global__ void k_pool2_bwd_v(const uint4* __restrict__ dy, uint4* __restrict__ dx, int N, int D, int H, int W, int C8,
+                              int accumulate) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= static_cast<int64_t>(N) * D * H * W * C8) return;
+  const int c = static_cast<int>(i % C8);
+  const Vox p = vox_of(i / C8, D, H, W);
+  const int d = D / 2, h = H / 2, w = W / 2;
+  float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  add8(a, dy[((((static_cast<int64_t>(p.n) * d + p.z / 2) * h + p.y / 2) * w + p.x / 2) * C8) + c]);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] *= 0.125f;
+  if (accumulate) add8(a, dx[i]);
+  dx[i] = pack8(a, 1.f);
+}
+
+__global__ void k_up2_v(const uint4* __restrict__ x, uint4* __restrict__ y, int N, int d, int h, int w, int C8, int Cy8,
+                        int off8) {
+  const int D = 2 * d, H = 2 * h, W = 2 * w;
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= static_cast<int64_t>(N) * D * H * W * C8) return;
+  const int c = static_cast<int>(i % C8);
+  const int64_t v = i / C8;
+  const Vox p = vox_of(v, D, H, W);
+  y[v * Cy8 + off8 + c] = x[((((static_cast<int64_t>(p.n) * d + p.z / 2) * h + p.y / 2) * w + p.x / 2) * C8) + c];
+}
+
+__global__ void k_up2_bwd_v(const uint4* __restrict__ dy, uint4* __restrict__ dx, int N, int d, int h, int w, int C8,
+                            int Cy8, int off8) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= static_cast<int64_t>(N) * d * h * w * C8) return;
+  const int c = static_cast<int>(i % C8);
+  const Vox p = vox_of(i / C8, d, h, w);
+  const int D = 2 * d, H = 2 * h, W = 2 * w;
+  float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int k = 0; k < 8; ++k) {
+    const int z = 2 * p.z + (k >> 2), yy = 2 * p.y + ((k >> 1) & 1), xx = 2 * p.x + (k & 1);
+    add8(a, dy[((((static_cast<int64_t>(p.n) * D + z) * H + yy) * W + xx) * Cy8) + off8 + c]);
+  }
+  dx[i] = pack8(a, 1.f);
+}
+
+__global__ void k_copy_channels_v(const uint4* __restrict__ src, uint4* __restrict__ dst, int64_t voxels, int C8,
+                                  int Cy8, int off8, int back) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= voxels * C8) return;
+  const int64_t v = i / C8;
+  const int c = static_cast<int>(i % C8);
+  if (back)
+    dst[i] = src[v * Cy8 + off8 + c];
+  else
+    dst[v * Cy8 + off8 + c] = src[i];
+}
+
 __global__ void k_copy_channels(const bf16* __restrict__ src, bf16* __restrict__ dst, int64_t voxels, int C, int Cy,
                                 int off, int back) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -644,6 +733,17 @@ mach_status mach_nn_pool2(const void* x, void* y, int32_t n, int32_t nz, int32_t
                           int32_t backward, int32_t accumulate, void* stream) {
   if (!x || !y || n < 1 || nz < 2 || ny < 2 || nx < 2 || nz % 2 || ny % 2 || nx % 2 || c < 1) return MACH_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (c % 8 == 0 && aligned16(x) && aligned16(y)) {
+    const int c8 = c / 8;
+    const int64_t tot = backward ? static_cast<int64_t>(n) * nz * ny * nx * c8
+                                 : static_cast<int64_t>(n) * (nz / 2) * (ny / 2) * (nx / 2) * c8;
+    if (!backward)
+      k_pool2_v<<<nblocks(tot), 256, 0, s>>>(static_cast<const uint4*>(x), static_cast<uint4*>(y), n, nz, ny, nx, c8);
+    else
+      k_pool2_bwd_v<<<nblocks(tot), 256, 0, s>>>(static_cast<const uint4*>(x), static_cast<uint4*>(y), n, nz, ny, nx,
+                                                 c8, accumulate);
+    return last_status();
+  }
   if (!backward) {
     const int64_t tot = static_cast<int64_t>(n) * (nz / 2) * (ny / 2) * (nx / 2) * c;
     k_pool2<<<nblocks(tot), 256, 0, s>>>(static_cast<const bf16*>(x), static_cast<bf16*>(y), n, nz, ny, nx, c);
@@ -659,6 +759,19 @@ mach_status mach_nn_up2(const void* x, void* y, int32_t n, int32_t nz, int32_t n
                         int32_t off, int32_t backward, void* stream) {
   if (!x || !y || n < 1 || nz < 1 || ny < 1 || nx < 1 || c < 1 || off < 0 || off + c > cy) return MACH_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (c % 8 == 0 && cy % 8 == 0 && off % 8 == 0 && aligned16(x) && aligned16(y)) {
+    const int c8 = c / 8, cy8 = cy / 8, off8 = off / 8;
+    if (!backward) {
+      const int64_t tot = static_cast<int64_t>(n) * 8 * nz * ny * nx * c8;
+      k_up2_v<<<nblocks(tot), 256, 0, s>>>(static_cast<const uint4*>(x), static_cast<uint4*>(y), n, nz, ny, nx, c8, cy8,
+                                           off8);
+    } else {
+      const int64_t tot = static_cast<int64_t>(n) * nz * ny * nx * c8;
+      k_up2_bwd_v<<<nblocks(tot), 256, 0, s>>>(static_cast<const uint4*>(x), static_cast<uint4*>(y), n, nz, ny, nx, c8,
+                                               cy8, off8);
+    }
+    return last_status();
+  }
   if (!backward) {
     const int64_t tot = static_cast<int64_t>(n) * 8 * nz * ny * nx * c;
     k_up2<<<nblocks(tot), 256, 0, s>>>(static_cast<const bf16*>(x), static_cast<bf16*>(y), n, nz, ny, nx, c, cy, off);
@@ -673,6 +786,11 @@ mach_status mach_nn_up2(const void* x, void* y, int32_t n, int32_t nz, int32_t n
 mach_status mach_nn_copy_channels(const void* src, void* dst, int64_t voxels, int32_t c, int32_t cy, int32_t off,
                                   int32_t back, void* stream) {
   if (!src || !dst || voxels < 1 || c < 1 || off < 0 || off + c > cy) return MACH_ERR_INVALID_ARG;
+  if (c % 8 == 0 && cy % 8 == 0 && off % 8 == 0 && aligned16(src) && aligned16(dst)) {
+    k_copy_channels_v<<<nblocks(voxels * (c / 8)), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const uint4*>(src), static_cast<uint4*>(dst), voxels, c / 8, cy / 8, off / 8, back);
+    return last_status();
+  }
   k_copy_channels<<<nblocks(voxels * c), 256, 0, static_cast<cudaStream_t>(stream)>>>(
       static_cast<const bf16*>(src), static_cast<bf16*>(dst), voxels, c, cy, off, back);
   return last_status();

@@ -215,6 +215,27 @@ def test_pool_upsample_copy_and_adjoints():
     np.testing.assert_array_equal(out.cpu().double().numpy(), gcath[..., 8:24])
 
 
+def test_data_movement_scalar_paths():
+    # channel counts and offsets that are not multiples of 8 take the element-wise kernels
+    nn = _nn()
+    r = np.random.default_rng(14)
+    x, xh = _bf(r.standard_normal((1, 4, 2, 6, 5)))
+    p = torch.empty((1, 2, 1, 3, 5), dtype=torch.bfloat16, device=dev)
+    nn.mach_nn_pool2(x, p)
+    assert _ulp_close(p.cpu().double().numpy(), U.pool2(xh))
+    src, srch = _bf(r.standard_normal((1, 2, 1, 3, 5)))
+    cat = torch.zeros((1, 4, 2, 6, 13), dtype=torch.bfloat16, device=dev)
+    nn.mach_nn_up2(src, cat, off=3)
+    np.testing.assert_array_equal(cat.cpu().double().numpy()[..., 3:8], U.up2(srch))
+    back = torch.empty((1, 2, 1, 3, 5), dtype=torch.bfloat16, device=dev)
+    gcat, gcath = _bf(r.standard_normal((1, 4, 2, 6, 13)))
+    nn.mach_nn_up2(gcat, back, off=3, backward=True)
+    assert _ulp_close(back.cpu().double().numpy(), U.up2_adjoint(gcath[..., 3:8]), 2.0 ** -20)
+    out = torch.empty((1, 4, 2, 6, 5), dtype=torch.bfloat16, device=dev)
+    nn.mach_nn_copy_channels(gcat, out, off=7, back=True)
+    np.testing.assert_array_equal(out.cpu().double().numpy(), gcath[..., 7:12])
+
+
 def test_lrelu_backward_and_bias_gradient():
     nn = _nn()
     r = np.random.default_rng(12)
