@@ -257,3 +257,32 @@ class UNet:
     def train_step(self, x, target, lr: float, loss=None, stream=None):
         _check(_L().mach_unet_train_step(self.handle, self._vol(x, "x"), self._vol(target, "target"), float(lr),
                                          _f32(loss, "loss"), _stream_ptr(stream)), "mach_unet_train_step")
+
+
+def _conv_case(argv) -> None:
+    """`python -m paper_2604_06257_gb300.nn conv CI CO SIDE BATCH [REPEAT]`: run one tensor-core
+    convolution on random bfloat16 data (a fixed launch for profilers)."""
+    import torch
+    from . import build
+    build.build()
+    ci, co, side, batch = (int(a) for a in argv[:4])
+    repeat = int(argv[4]) if len(argv) > 4 else 4
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(batch, side, side, side, ci, device="cuda", generator=g).to(torch.bfloat16)
+    w = torch.randn(27, ci, co, device="cuda", generator=g) * 0.05
+    wpk, _ = mach_nn_pack_weights(w, ci, co, flipped=False)
+    y = torch.empty(batch, side, side, side, co, device="cuda", dtype=torch.bfloat16)
+    for _ in range(repeat):
+        mach_nn_conv3d_tc(x, wpk, co, None, y, None)
+    torch.cuda.synchronize()
+    if mach_nn_device_status() != 0:
+        raise MachError(5, "mach_nn_conv3d_tc")
+    print(f"conv {ci}->{co} on {batch} x {side}^3: ok")
+
+
+if __name__ == "__main__":
+    import sys
+    if len(sys.argv) > 1 and sys.argv[1] == "conv":
+        _conv_case(sys.argv[2:])
+    else:
+        raise SystemExit("usage: python -m paper_2604_06257_gb300.nn conv CI CO SIDE BATCH [REPEAT]")
