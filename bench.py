@@ -488,10 +488,11 @@ def run_ragged(args):
 # ------------------------------------------------------- learned compounding ----
 
 def run_learned(args):
-    """Learned compounding at 128^3 (matrix array, 1024 elements, 8 scenes per batch on the
-    frame axis): 3-angle DAS followed by the trained U-Net, against plain 21-angle DAS of
-    the same scenes.  Value = volumes/s of the learned path; both paths' errors against
-    the 21-angle volumes on held-out scenes are reported with it."""
+    """Learned compounding at 128^3 (matrix array, 1024 elements, 32 scenes per batch on the
+    frame axis, split complex64 IQ rows for both paths): 3-angle DAS followed by the
+    trained U-Net, against plain 21-angle DAS of the same scenes.  Value = volumes/s of
+    the learned path; both paths' errors against the 21-angle volumes on held-out scenes
+    are reported with it."""
     import numpy as np
     import torch
     import oracle
@@ -506,7 +507,7 @@ def run_learned(args):
         raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
     pkg_build.build()
     m.lib()
-    n, B, nblk = 128, 8, 32
+    n, B, nblk = 128, 32, 64
     V = n ** 3
     params, gain, levels, base = Lc.load(os.path.join(Lc.WEIGHTS_DIR, "unet_few3_many21_128.npz"))
     # held-out scenes: blocks never used in training, complex-weighted, one scene per frame
@@ -517,8 +518,13 @@ def run_learned(args):
     Wsc = torch.as_tensor(Lc.scene_weights(np.random.default_rng(99), nblk, B)).cuda()
     iq = (iq_blk.view(-1, nblk) @ Wsc).view(T, C, S, B).contiguous()
     del iq_blk
-    iq_few = iq.index_select(0, torch.tensor(Lc.FEW_IN_MANY, device="cuda")).contiguous()
-    acq_many, acq_few = Lc.acquisition(n, B, "many"), Lc.acquisition(n, B, "few")
+    # the scanner's order [F][T][C][S] for the end-to-end leg; the kernels' split rows
+    # (K0, outside the timed region) for the device-resident legs
+    few_scanner = iq.index_select(0, torch.tensor(Lc.FEW_IN_MANY, device="cuda")).permute(3, 0, 1, 2).contiguous()
+    iq_few = m.prepare_iq(few_scanner, "ftcs", "c64split")
+    iq = m.prepare_iq(iq.permute(3, 0, 1, 2).contiguous(), "ftcs", "c64split")
+    acq_many = Lc.acquisition(n, B, "many").replace(iq_dtype="c64split")
+    acq_few = Lc.acquisition(n, B, "few").replace(iq_dtype="c64split")
     pm, pf = m.Plan(**m.plan_kwargs(acq_many)), m.Plan(**m.plan_kwargs(acq_few))
     net = UNet(n, n, n, B, levels=levels, base_ch=base)
     net.set_params(params)
@@ -577,15 +583,18 @@ def run_learned(args):
     L = levels
     unet_launches = 2 + (L - 1) + 2 * L + 4 * (L - 1) + 2
 
-    # end to end through the public API: the 3-angle IQ from pinned host memory, the
-    # prediction back to pinned host memory, copies inside the timed region
-    iq_pin = iq_few.cpu().pin_memory()
+    # end to end through the public API: the 3-angle IQ in the scanner's order from pinned
+    # host memory, K0 to split rows, DAS, U-Net, the prediction back to pinned host
+    # memory; copies inside the timed region
+    iq_pin = few_scanner.cpu().pin_memory()
     out_pin = torch.empty((V, B), dtype=torch.complex64).pin_memory()
-    iq_dev = torch.empty_like(iq_few)
+    scan_dev = torch.empty_like(few_scanner)
+    Tf = len(Lc.FEW_IN_MANY)
 
     def e2e_step():
-        iq_dev.copy_(iq_pin, non_blocking=True)
-        pf.run(iq_dev, y_few)
+        scan_dev.copy_(iq_pin, non_blocking=True)
+        m.mach_iq_convert(scan_dev, "ftcs", iq_few, "c64split", Tf, C, S, B)
+        pf.run(iq_few, y_few)
         net.forward(y_few, pred)
         out_pin.copy_(pred, non_blocking=True)
 
@@ -603,8 +612,8 @@ def run_learned(args):
     cpu = None
     if not args.no_cpu_baseline:
         h = n // 2
-        sub = acq_few.replace(n_frames=1)
-        iq1 = iq_few[..., :1].contiguous().cpu()
+        sub = acq_few.replace(n_frames=1, iq_dtype="c64")
+        iq1 = few_scanner[:1].permute(1, 2, 3, 0).contiguous().cpu()
         g = np.arange(h) + h // 2
         idx = (g[None, None, :] + n * (g[None, :, None] + n * g[:, None, None])).ravel()
         t0 = time.perf_counter()
@@ -622,7 +631,8 @@ def run_learned(args):
             "ms_per_step": t_learned * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 DAS, bf16 U-Net (f32 accumulate)", "data": "synthetic",
             "config": {"workload": f"learned compounding: 32x32 matrix array (1024 el, fc 7.8 MHz, fs 31.2 MHz), "
-                                   f"{n}^3 voxels at 0.1 mm, {B} scenes per batch, 3 plane waves "
+                                   f"{n}^3 voxels at 0.1 mm, {B} scenes per batch (frame axis, split complex64 IQ "
+                                   "rows for both paths), 3 plane waves "
                                    "(az -10/0/10 deg) + U-Net (4 levels, 16-128 ch, 3x3x3, bf16) vs 21 plane "
                                    "waves (az/el cross, -10..10 deg)",
                        "l2": "flushed between timed steps (256 MB write, outside the timed events)",
