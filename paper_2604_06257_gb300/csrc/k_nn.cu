@@ -534,18 +534,39 @@ __global__ void k_to_bf16(const float* __restrict__ w, int64_t n, bf16* __restri
 }
 
 // ------------------------------------------------------------ network boundary ----
-__global__ void k_vol_sumsq(const float2* __restrict__ y, float* __restrict__ sums, int64_t V, int N) {
-  __shared__ float part[256];
-  for (int n = threadIdx.x; n < N; n += blockDim.x) part[n] = 0.f;
+// Sum of |y|^2 per volume in a fixed order (no atomics), so a volume's RMS does not
+// depend on the other volumes of the batch or on scheduling.  Pass 1: block b sums its
+// contiguous voxel range; thread t owns volume t % N of rows t / N (+ stride), partial sums
+// meet in shared memory in thread order.  Pass 2: one thread per volume adds the blocks.
+__global__ void k_vol_sumsq_part(const float2* __restrict__ y, float* __restrict__ part, int64_t V, int N,
+                                 int64_t rows_per_block) {
+  __shared__ float red[256];
+  const int tid = threadIdx.x;
+  const int lanes = 256 / N;   // threads per volume
+  const int n = tid % N, r = tid / N;
+  const int64_t v0 = static_cast<int64_t>(blockIdx.x) * rows_per_block;
+  const int64_t v1 = v0 + rows_per_block < V ? v0 + rows_per_block : V;
+  float acc = 0.f;
+  if (r < lanes)
+    for (int64_t v = v0 + r; v < v1; v += lanes) {
+      const float2 a = y[v * N + n];
+      acc = fmaf(a.x, a.x, fmaf(a.y, a.y, acc));
+    }
+  red[tid] = acc;
   __syncthreads();
-  const int64_t total = V * N;
-  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const float2 a = y[i];
-    atomicAdd(&part[i % N], fmaf(a.x, a.x, a.y * a.y));
+  if (tid < N) {
+    float s = 0.f;
+    for (int k = 0; k < lanes; ++k) s += red[k * N + tid];
+    part[static_cast<int64_t>(blockIdx.x) * N + tid] = s;
   }
-  __syncthreads();
-  for (int n = threadIdx.x; n < N; n += blockDim.x) atomicAdd(&sums[n], part[n]);
+}
+
+__global__ void k_vol_sumsq_final(const float* __restrict__ part, float* __restrict__ sums, int blocks, int N) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float s = 0.f;
+  for (int b = 0; b < blocks; ++b) s += part[static_cast<int64_t>(b) * N + n];
+  sums[n] = s;
 }
 
 __device__ __forceinline__ float rms_of(const float* sums, int n, int64_t V) {
@@ -606,10 +627,11 @@ namespace {
 inline unsigned blocks_for(int64_t n, int b = 256) { return static_cast<unsigned>((n + b - 1) / b); }
 }  // namespace
 
-cudaError_t launch_vol_sumsq(const float2* y, float* sums, int64_t V, int N, cudaStream_t s) {
-  const int64_t total = V * N;
-  const unsigned grid = total < 152LL * 4 * 256 ? blocks_for(total) : 152u * 4u;
-  k_vol_sumsq<<<grid, 256, 0, s>>>(y, sums, V, N);
+cudaError_t launch_vol_sumsq(const float2* y, float* sums, float* part, int64_t V, int N, cudaStream_t s) {
+  const int64_t rows = (V + kSumBlocks - 1) / kSumBlocks;
+  const int blocks = static_cast<int>((V + rows - 1) / rows);
+  k_vol_sumsq_part<<<blocks, 256, 0, s>>>(y, part, V, N, rows);
+  k_vol_sumsq_final<<<(N + 127) / 128, 128, 0, s>>>(part, sums, blocks, N);
   return cudaGetLastError();
 }
 

@@ -9,8 +9,10 @@ namespace mach_nn {
 
 constexpr float kLeak = 1.0f / 64.0f;   // leaky-ReLU slope (exact in every format used)
 
-// sums[n] += sum_v |y[v][n]|^2 for complex64 y [V][N]  (caller zeroes sums)
-cudaError_t launch_vol_sumsq(const float2* y, float* sums, int64_t V, int N, cudaStream_t s);
+// sums[n] = sum_v |y[v][n]|^2 for complex64 y [V][N] (N <= 256), in a fixed order;
+// part: scratch of kSumBlocks * N floats
+constexpr int kSumBlocks = 608;
+cudaError_t launch_vol_sumsq(const float2* y, float* sums, float* part, int64_t V, int N, cudaStream_t s);
 
 // x = y / rms: xin bf16 [N][V][C] (channels 0, 1 = re, im; the rest 0), xf float [N][V][2]
 cudaError_t launch_pack(const float2* y, const float* sums, int64_t V, int N, int C, void* xin, float* xf,

@@ -62,6 +62,7 @@ struct mach_unet_s {
   void* g_o = nullptr;    // bfloat16 [N][V0][c0]
   float* xf = nullptr;    // float32 [N][V0][2]
   float* sums = nullptr;  // float32 [N]
+  float* sum_part = nullptr;  // float32 [kSumBlocks][N] (fixed-order RMS reduction)
   float* params = nullptr;
   float* grads = nullptr;
   float* adam_m = nullptr;
@@ -117,8 +118,7 @@ mach_status conv_bwd(mach_unet_s* u, const Conv& c, void* gout, void* gin, cudaS
 
 mach_status forward(mach_unet_s* u, const void* x, cudaStream_t s) {
   const int L = u->L, N = u->N;
-  TRY(cuda_ok(cudaMemsetAsync(u->sums, 0, sizeof(float) * N, s)));
-  TRY(cuda_ok(launch_vol_sumsq(static_cast<const float2*>(x), u->sums, u->vox1(0), N, s)));
+  TRY(cuda_ok(launch_vol_sumsq(static_cast<const float2*>(x), u->sums, u->sum_part, u->vox1(0), N, s)));
   TRY(cuda_ok(launch_pack(static_cast<const float2*>(x), u->sums, u->vox1(0), N, u->c0, u->in[0].p, u->xf, s)));
   for (int l = 0; l < L; ++l) {
     if (l > 0)
@@ -303,6 +303,7 @@ mach_status mach_unet_create(const mach_unet_desc* desc, uint64_t seed, mach_une
   want(&u->g_o, 2 * static_cast<size_t>(u->vox(0)) * u->c0);
   want(reinterpret_cast<void**>(&u->xf), sizeof(float) * 2 * static_cast<size_t>(u->vox(0)));
   want(reinterpret_cast<void**>(&u->sums), sizeof(float) * 256);
+  want(reinterpret_cast<void**>(&u->sum_part), sizeof(float) * kSumBlocks * 256);
   size_t total = 0;
   for (const Req& r : reqs) total += r.bytes;
   if (cudaMalloc(&u->arena, total) != cudaSuccess) {
