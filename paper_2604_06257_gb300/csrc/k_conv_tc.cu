@@ -414,20 +414,31 @@ struct TcShape {
   size_t smem;
 };
 
-TcShape tc_shape(int ci, int co) {
+TcShape shape_for(int ci, int co, int tz) {
   TcShape t{};
-  t.tz = co <= 128 ? 2 : 1;                          // two accumulators x two buffers fit 512 columns
-  const uint32_t halo = static_cast<uint32_t>(kHX * kHY * (t.tz + 2) * 16);
+  t.tz = tz;
+  const uint32_t halo = static_cast<uint32_t>(kHX * kHY * (tz + 2) * 16);
   t.group_pitch = (halo + 127u) & ~127u;              // TMA destinations are 128-byte aligned
   const uint32_t tap = 32u * static_cast<uint32_t>(co);
   const uint32_t all = 27u * static_cast<uint32_t>(ci / 16) * tap;
   t.resident = all <= kResidentMax ? 1 : 0;
   t.w_bytes = t.resident ? all : kNB * 9u * tap;
   uint32_t c = 32;
-  while (c < 2u * static_cast<uint32_t>(t.tz * co)) c <<= 1;
+  while (c < 2u * static_cast<uint32_t>(tz * co)) c <<= 1;
   t.tmem_cols = c;
   t.smem = 1024 + 4 * static_cast<size_t>(t.group_pitch) + t.w_bytes + 8 * 13 + 16;
   return t;
+}
+
+// z planes per tile: more planes share one halo load and its waits, as long as two CTAs
+// still fit an SM (shared memory) and tz planes x two buffers of co columns fit the 512
+// tensor-memory columns
+TcShape tc_shape(int ci, int co) {
+  if (co <= 32) {
+    const TcShape t4 = shape_for(ci, co, 4);
+    if (t4.smem <= 110 * 1024) return t4;
+  }
+  return shape_for(ci, co, co <= 128 ? 2 : 1);
 }
 
 }  // namespace
@@ -473,8 +484,9 @@ cudaError_t launch_conv_tc(const void* x, const void* wpk, const float* bias, vo
   p.tmem_cols = shp.tmem_cols;
   p.wait_limit = kDefaultWait;
   const size_t smem = shp.smem;
-  auto kern = flip ? (shp.tz == 2 ? k_conv3d_tc<true, 2> : k_conv3d_tc<true, 1>)
-                  : (shp.tz == 2 ? k_conv3d_tc<false, 2> : k_conv3d_tc<false, 1>);
+  auto kern = flip ? (shp.tz == 4 ? k_conv3d_tc<true, 4> : shp.tz == 2 ? k_conv3d_tc<true, 2> : k_conv3d_tc<true, 1>)
+                  : (shp.tz == 4 ? k_conv3d_tc<false, 4>
+                                 : shp.tz == 2 ? k_conv3d_tc<false, 2> : k_conv3d_tc<false, 1>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
