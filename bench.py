@@ -526,7 +526,7 @@ def run_learned(args):
     acq_many = Lc.acquisition(n, B, "many").replace(iq_dtype="c64split")
     acq_few = Lc.acquisition(n, B, "few").replace(iq_dtype="c64split")
     pm, pf = m.Plan(**m.plan_kwargs(acq_many)), m.Plan(**m.plan_kwargs(acq_few))
-    net = UNet(n, n, n, B, levels=levels, base_ch=base)
+    net = UNet(n, n, n, B, levels=levels, base_ch=base, inference_only=True)
     net.set_params(params)
     net.set_gain(gain)
     y_many = torch.empty((V, B), dtype=torch.complex64, device="cuda")

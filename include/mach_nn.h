@@ -123,6 +123,9 @@ typedef struct {
     int32_t base_ch;    /* c0, a multiple of 16 (16)                               */
     int32_t batch;      /* N volumes per call                                      */
     int32_t nx, ny, nz; /* volume dimensions, multiples of 2^(L-1)                 */
+    int32_t inference_only; /* non-zero: no gradient, optimiser or data-gradient buffers
+                               (about half the memory); backward / train_step then return
+                               MACH_ERR_UNSUPPORTED */
 } mach_unet_desc;
 
 typedef struct {

@@ -27,6 +27,7 @@
 
 #include <cstdint>
 #include <mutex>
+#include <unordered_map>
 
 #include "async_copy.cuh"
 #include "mach_nn.h"
@@ -443,6 +444,63 @@ TcShape tc_shape(int ci, int co) {
 
 }  // namespace
 
+// Per-kernel launch set-up, done once per (device, instantiation) and cached, so that a
+// launch makes no runtime calls besides the launch itself (and can be captured in a CUDA
+// graph): the dynamic shared-memory limit and carve-out, and the resident CTAs per SM from
+// shared memory (1 KB reserved per CTA), registers (allocated per warp in units of 256) and
+// tensor memory (512 columns per SM; a CTA beyond that would wait in allocation).
+cudaError_t kernel_setup(const void* kern, size_t smem, uint32_t tmem_cols, int* per_sm, int* sms) {
+  struct Entry {
+    size_t smem_set;
+    int regs;
+  };
+  struct Dev {
+    int sms, smem_sm, regs_sm;
+  };
+  static std::mutex mu;
+  static std::unordered_map<const void*, Entry> kernels[64];
+  static Dev devs[64];
+  static bool dev_known[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!dev_known[dev]) {
+    Dev d{};
+    if ((e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&d.smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+      return e;
+    if ((e = cudaDeviceGetAttribute(&d.regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess)
+      return e;
+    devs[dev] = d;
+    dev_known[dev] = true;
+  }
+  auto it = kernels[dev].find(kern);
+  if (it == kernels[dev].end()) {
+    cudaFuncAttributes fa{};
+    if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return e;
+    it = kernels[dev].emplace(kern, Entry{0, fa.numRegs}).first;
+  }
+  if (it->second.smem_set < smem) {
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem))) !=
+        cudaSuccess)
+      return e;
+    it->second.smem_set = smem;
+  }
+  const Dev& d = devs[dev];
+  const int by_smem = d.smem_sm / static_cast<int>(smem + 1024);
+  const int regs_warp = ((it->second.regs * 32 + 255) / 256) * 256;
+  const int by_regs = d.regs_sm / (regs_warp * (kThreads / 32));
+  const int by_tmem = static_cast<int>(512 / tmem_cols);
+  int n = by_smem < by_regs ? by_smem : by_regs;
+  n = n < by_tmem ? n : by_tmem;
+  *per_sm = n < 1 ? 1 : n;
+  *sms = d.sms;
+  return cudaSuccess;
+}
+
 bool conv_tc_supported(int ci, int co) { return ci >= 16 && ci % 16 == 0 && co >= 16 && co % 16 == 0 && co <= 256; }
 
 cudaError_t launch_conv_tc(const void* x, const void* wpk, const float* bias, void* y, float* yf, int n, int d,
@@ -487,28 +545,9 @@ cudaError_t launch_conv_tc(const void* x, const void* wpk, const float* bias, vo
   auto kern = flip ? (shp.tz == 4 ? k_conv3d_tc<true, 4> : shp.tz == 2 ? k_conv3d_tc<true, 2> : k_conv3d_tc<true, 1>)
                   : (shp.tz == 4 ? k_conv3d_tc<false, 4>
                                  : shp.tz == 2 ? k_conv3d_tc<false, 2> : k_conv3d_tc<false, 1>);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  int per_sm = 0, sms = 0;
+  const cudaError_t e = kernel_setup(reinterpret_cast<const void*>(kern), smem, p.tmem_cols, &per_sm, &sms);
   if (e != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
-    return e;
-  int dev = 0, sms = 0, smem_sm = 0, regs_sm = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
-    return e;
-  if ((e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess) return e;
-  cudaFuncAttributes fa{};
-  if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
-  // resident CTAs per SM: shared memory (1 KB reserved per CTA), registers (allocated per
-  // warp in units of 256), and tensor memory (512 columns per SM; a CTA beyond that would
-  // wait in allocation)
-  const int by_smem = smem_sm / static_cast<int>(smem + 1024);
-  const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
-  const int by_regs = regs_sm / (regs_warp * (kThreads / 32));
-  const int by_tmem = static_cast<int>(512 / p.tmem_cols);
-  int per_sm = by_smem < by_regs ? by_smem : by_regs;
-  per_sm = per_sm < by_tmem ? per_sm : by_tmem;
-  per_sm = per_sm < 1 ? 1 : per_sm;
   const int64_t grid = p.tiles < static_cast<int64_t>(sms) * per_sm ? p.tiles : static_cast<int64_t>(sms) * per_sm;
   kern<<<static_cast<unsigned>(grid), kThreads, smem, s>>>(map, p);
   return cudaGetLastError();

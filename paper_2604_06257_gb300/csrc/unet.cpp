@@ -73,6 +73,7 @@ struct mach_unet_s {
   float gain = 1.f;
   int step = 0;
   int backend = MACH_UNET_TCGEN05;
+  bool training = true;
 
   int ch(int l) const { return c0 << l; }
   int64_t vox(int l) const { return static_cast<int64_t>(N) * nz[l] * ny[l] * nx[l]; }
@@ -199,6 +200,7 @@ mach_status mach_unet_create(const mach_unet_desc* desc, uint64_t seed, mach_une
   mach_unet_s* u = new (std::nothrow) mach_unet_s;
   if (!u) return MACH_ERR_OOM;
   u->d = d;
+  u->training = d.inference_only == 0;
   u->L = d.levels;
   u->c0 = d.base_ch;
   u->N = d.batch;
@@ -272,21 +274,27 @@ mach_status mach_unet_create(const mach_unet_desc* desc, uint64_t seed, mach_une
   std::vector<Req> reqs;
   auto want = [&](void** slot, size_t bytes) { reqs.push_back({slot, (bytes + 255) / 256 * 256}); };
   const size_t np = sizeof(float) * static_cast<size_t>(u->n_params);
+  const bool tr = u->training;
   want(reinterpret_cast<void**>(&u->params), np);
-  want(reinterpret_cast<void**>(&u->grads), np);
-  want(reinterpret_cast<void**>(&u->adam_m), np);
-  want(reinterpret_cast<void**>(&u->adam_v), np);
+  if (tr) {
+    want(reinterpret_cast<void**>(&u->grads), np);
+    want(reinterpret_cast<void**>(&u->adam_m), np);
+    want(reinterpret_cast<void**>(&u->adam_v), np);
+  }
   for (Conv& c : u->convs) {
     want(&c.wb, 2 * 27 * static_cast<size_t>(c.ci) * c.co);
-    want(&c.wbt, 2 * 27 * static_cast<size_t>(c.ci) * c.co);
     want(&c.wpk, 2 * 27 * static_cast<size_t>(c.ci) * c.co);
-    want(&c.wpkt, 2 * 27 * static_cast<size_t>(c.ci) * c.co);
+    if (tr) {
+      want(&c.wbt, 2 * 27 * static_cast<size_t>(c.ci) * c.co);
+      want(&c.wpkt, 2 * 27 * static_cast<size_t>(c.ci) * c.co);
+    }
   }
   auto want_act = [&](Act& t) { want(&t.p, 2 * static_cast<size_t>(u->vox(t.level)) * t.C); };
   for (int l = 0; l < L; ++l) {
     want_act(u->in[l]);
     want_act(u->a[l]);
     want_act(u->e[l]);
+    if (!tr) continue;
     if (l > 0) want_act(u->g_in[l]);
     want_act(u->g_a[l]);
     want_act(u->g_e[l]);
@@ -295,12 +303,13 @@ mach_status mach_unet_create(const mach_unet_desc* desc, uint64_t seed, mach_une
     want_act(u->cat[l]);
     want_act(u->b[l]);
     want_act(u->dd[l]);
+    if (!tr) continue;
     want_act(u->g_cat[l]);
     want_act(u->g_b[l]);
     want_act(u->g_d[l]);
   }
   want(reinterpret_cast<void**>(&u->o), sizeof(float) * static_cast<size_t>(u->vox(0)) * u->c0);
-  want(&u->g_o, 2 * static_cast<size_t>(u->vox(0)) * u->c0);
+  if (tr) want(&u->g_o, 2 * static_cast<size_t>(u->vox(0)) * u->c0);
   want(reinterpret_cast<void**>(&u->xf), sizeof(float) * 2 * static_cast<size_t>(u->vox(0)));
   want(reinterpret_cast<void**>(&u->sums), sizeof(float) * 256);
   want(reinterpret_cast<void**>(&u->sum_part), sizeof(float) * kSumBlocks * 256);
@@ -367,6 +376,7 @@ mach_status mach_unet_get_params(mach_unet net, float* host, int64_t count) {
 
 mach_status mach_unet_get_grads(mach_unet net, float* host, int64_t count) {
   if (!net || !host || count != net->n_params) return MACH_ERR_INVALID_ARG;
+  if (!net->training) return MACH_ERR_UNSUPPORTED;
   return cuda_ok(cudaMemcpy(host, net->grads, sizeof(float) * count, cudaMemcpyDeviceToHost));
 }
 
@@ -374,8 +384,10 @@ mach_status mach_unet_set_params(mach_unet net, const float* host, int64_t count
   if (!net || !host || count != net->n_params) return MACH_ERR_INVALID_ARG;
   const size_t bytes = sizeof(float) * static_cast<size_t>(count);
   TRY(cuda_ok(cudaMemcpy(net->params, host, bytes, cudaMemcpyHostToDevice)));
-  TRY(cuda_ok(cudaMemset(net->adam_m, 0, bytes)));
-  TRY(cuda_ok(cudaMemset(net->adam_v, 0, bytes)));
+  if (net->training) {
+    TRY(cuda_ok(cudaMemset(net->adam_m, 0, bytes)));
+    TRY(cuda_ok(cudaMemset(net->adam_v, 0, bytes)));
+  }
   net->step = 0;
   TRY(refresh_bf16(net, nullptr));
   return cuda_ok(cudaDeviceSynchronize());
@@ -403,6 +415,7 @@ mach_status mach_unet_forward(mach_unet net, const void* x, void* y, void* strea
 
 mach_status mach_unet_backward(mach_unet net, const void* x, const void* target, float* loss, void* stream) {
   if (!net || !x || !target) return MACH_ERR_INVALID_ARG;
+  if (!net->training) return MACH_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   TRY(forward(net, x, s));
   return backward(net, target, loss, s);
@@ -411,6 +424,7 @@ mach_status mach_unet_backward(mach_unet net, const void* x, const void* target,
 mach_status mach_unet_train_step(mach_unet net, const void* x, const void* target, float lr, float* loss,
                                  void* stream) {
   if (!net || !x || !target || !(lr >= 0.f)) return MACH_ERR_INVALID_ARG;
+  if (!net->training) return MACH_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   TRY(forward(net, x, s));
   TRY(backward(net, target, loss, s));

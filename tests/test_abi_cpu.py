@@ -140,7 +140,7 @@ def test_network_entry_points_reject_bad_arguments_before_cuda():
                     ((4, 16, 1, 12, 8, 8), m.MACH_ERR_INVALID_ARG),     # nx not a multiple of 8
                     ((4, 16, 0, 8, 8, 8), m.MACH_ERR_INVALID_ARG),      # empty batch
                     ((4, 48, 1, 8, 8, 8), m.MACH_ERR_UNSUPPORTED)]:     # 384 channels at the bottom
-        assert L.mach_unet_create(C.byref(nn.mach_unet_desc(*d)), 0, C.byref(h)) == want, d
+        assert L.mach_unet_create(C.byref(nn.mach_unet_desc(*d, 0)), 0, C.byref(h)) == want, d
         assert not h.value
 
 

@@ -354,3 +354,57 @@ def test_fresh_network_predicts_gain_times_input_and_learns():
             net.train_step(yd, td, 2e-3, loss)
             hist.append(float(loss.item()))
     assert hist[-1] < 0.5 * hist[0], hist[::10]
+
+
+def test_inference_only_network_matches_and_refuses_training():
+    nn = _nn()
+    r = np.random.default_rng(31)
+    p = U.he_like(4, 16, r).astype(np.float32)
+    x = torch.as_tensor((r.standard_normal((16 * 16 * 16, 2)) + 1j * r.standard_normal((16 * 16 * 16, 2)))
+                        .astype(np.complex64)).to(dev)
+    with nn.UNet(16, 16, 16, 2) as full, nn.UNet(16, 16, 16, 2, inference_only=True) as lite:
+        assert lite.device_bytes < 0.6 * full.device_bytes
+        for net in (full, lite):
+            net.set_params(p)
+            net.set_gain(0.7)
+        a, b = full.forward(x), lite.forward(x)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+        loss = torch.zeros(1, device=dev)
+        with pytest.raises(Exception):
+            lite.train_step(x, x, 1e-3, loss)
+        with pytest.raises(Exception):
+            lite.grads()
+
+
+def test_das_and_network_replay_from_one_cuda_graph():
+    # the learned path (few-angle DAS, then the network) captured once and replayed: every
+    # launch is stream-ordered and nothing synchronises the host
+    nn = _nn()
+    import synth
+    import paper_2604_06257_gb300 as m
+    from paper_2604_06257_gb300 import learned as Lc
+    acq = Lc.acquisition(16, 8, "few", 512)
+    iq = synth.random_iq(acq, 9, device=dev)
+    r = np.random.default_rng(32)
+    with m.Plan(**m.plan_kwargs(acq)) as plan, nn.UNet(16, 16, 16, 8, inference_only=True) as net:
+        net.set_params(U.he_like(4, 16, r).astype(np.float32))
+        y = torch.empty((acq.n_vox, 8), dtype=torch.complex64, device=dev)
+        out = torch.empty_like(y)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            plan.run(iq, y, stream=s)
+            net.forward(y, out, stream=s)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        eager = out.clone()
+        out.zero_()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            plan.run(iq, y)
+            net.forward(y, out)
+        for _ in range(2):
+            g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, eager)
