@@ -48,7 +48,7 @@ typedef enum {
     MACH_ERR_INVALID_ARG = 1,   /* a NULL pointer, a size out of range, inconsistent geometry */
     MACH_ERR_CUDA = 2,          /* a CUDA runtime call or a launch failed                     */
     MACH_ERR_OOM = 3,           /* device allocation failed, or the plan would not fit        */
-    MACH_ERR_UNSUPPORTED = 4,   /* valid request outside what this build implements          */
+    MACH_ERR_UNSUPPORTED = 4,   /* valid request outside what this library implements        */
     MACH_ERR_TIMEOUT = 5        /* a bounded device-side wait gave up                         */
 } mach_status;
 
