@@ -488,7 +488,7 @@ def run_ragged(args):
 # ------------------------------------------------------- learned compounding ----
 
 def run_learned(args):
-    """Learned compounding at 128^3 (matrix array, 1024 elements, 32 scenes per batch on the
+    """Learned compounding at 128^3 (matrix array, 1024 elements, 64 scenes per batch on the
     frame axis, split complex64 IQ rows for both paths): 3-angle DAS followed by the
     trained U-Net, against plain 21-angle DAS of the same scenes.  Value = volumes/s of
     the learned path; both paths' errors against the 21-angle volumes on held-out scenes
@@ -507,7 +507,7 @@ def run_learned(args):
         raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
     pkg_build.build()
     m.lib()
-    n, B, nblk = 128, 32, 64
+    n, B, nblk = 128, 64, 64
     V = n ** 3
     params, gain, levels, base = Lc.load(os.path.join(Lc.WEIGHTS_DIR, "unet_few3_many21_128.npz"))
     # held-out scenes: blocks never used in training, complex-weighted, one scene per frame
