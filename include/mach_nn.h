@@ -79,6 +79,12 @@ mach_status mach_nn_pack_weights(const float* w, void* w_packed, void* w_packed_
  * convolution gave up a bounded wait since the last call, else MACH_OK. */
 mach_status mach_nn_device_status(void* stream);
 
+/* Test hook for the tensor-core convolution's bounded waits: with stall_copies != 0 its copy
+ * warp issues no copies, so every wait runs out; wait_limit = polls per wait (0: default).
+ * A stalled launch gives up, frees its tensor memory and sets the status that
+ * mach_nn_device_status reports; the context stays usable.  Not thread-safe. */
+void mach_nn_debug_conv(int32_t stall_copies, uint32_t wait_limit);
+
 /* Weight gradient, accumulated:  dw[tap, ci, co] += sum_{n,z,y,x} X[n, z+dz, y+dy, x+dx, ci] *
  * dY[n, z, y, x, co]   (float32 dw, caller zeroes it). */
 mach_status mach_nn_conv3d_wgrad(const void* x, const void* dy, float* dw, int32_t n, int32_t nz, int32_t ny,

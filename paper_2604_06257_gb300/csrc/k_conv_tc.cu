@@ -51,7 +51,9 @@ constexpr int kThreads = 192;
 constexpr uint32_t kDefaultWait = 1u << 24;
 constexpr uint32_t kResidentMax = 96 * 1024;                 // weights kept whole in shared memory
 
-__device__ int g_conv_tc_err;   // bit 0: a bounded wait gave up, bit 1: the final wait gave up
+__device__ int g_conv_tc_err;   // bit 0: a bounded wait gave up
+uint32_t g_wait_limit = 0;      // test hook: polls per bounded wait (0: default)
+int g_debug_stall = 0;          // test hook: see ConvTcParams::debug_stall, bit 1: the final wait gave up
 
 struct ConvTcParams {
   const bf16* wpk;      // packed weights [Ci/16][27][2][Co][8]
@@ -67,6 +69,7 @@ struct ConvTcParams {
   uint32_t group_pitch; // bytes between the two 8-channel groups of a halo stage
   uint32_t tmem_cols;
   uint32_t wait_limit;
+  int debug_stall;      // test hook: the copy warp issues nothing, so every wait runs out
 };
 
 // tcgen05 shared-memory matrix descriptor: no swizzle, start address, leading (K
@@ -198,7 +201,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_conv3d_tc(const __grid_constant
   };
 
   if (warp == 0) {
-    if (lane == 0) {   // ---------------------------------------------- copies
+    if (lane == 0 && !p.debug_stall) {   // ----------------------------- copies
       if (p.resident) {
         mbar_arrive_expect_tx(&fullB[0], w_bytes);
         bulk_g2s(sW, p.wpk, w_bytes, &fullB[0]);
@@ -540,7 +543,8 @@ cudaError_t launch_conv_tc(const void* x, const void* wpk, const float* bias, vo
   p.tiles = static_cast<int64_t>(p.tiles_x) * p.tiles_y * p.tiles_z * n;
   p.group_pitch = shp.group_pitch;
   p.tmem_cols = shp.tmem_cols;
-  p.wait_limit = kDefaultWait;
+  p.wait_limit = g_wait_limit ? g_wait_limit : kDefaultWait;
+  p.debug_stall = g_debug_stall;
   const size_t smem = shp.smem;
   auto kern = flip ? (shp.tz == 4 ? k_conv3d_tc<true, 4> : shp.tz == 2 ? k_conv3d_tc<true, 2> : k_conv3d_tc<true, 1>)
                   : (shp.tz == 4 ? k_conv3d_tc<false, 4>
@@ -589,6 +593,11 @@ mach_status mach_nn_conv3d_tc(const void* x, const void* wpk, const float* bias,
     return MACH_ERR_UNSUPPORTED;
   }
   return e == cudaSuccess ? MACH_OK : MACH_ERR_CUDA;
+}
+
+void mach_nn_debug_conv(int32_t stall_copies, uint32_t wait_limit) {
+  g_debug_stall = stall_copies ? 1 : 0;
+  g_wait_limit = wait_limit;
 }
 
 mach_status mach_nn_device_status(void* stream) {

@@ -15,6 +15,7 @@ import numpy as np
 from . import MachError, _dev_ptr, _stream_ptr, lib
 
 NN_EXPORTS = ("mach_nn_conv3d", "mach_nn_conv3d_tc", "mach_nn_pack_weights", "mach_nn_device_status",
+              "mach_nn_debug_conv",
               "mach_unet_set_backend", "mach_nn_conv3d_wgrad", "mach_nn_bias_grad", "mach_nn_lrelu_bwd",
               "mach_nn_pool2", "mach_nn_up2", "mach_nn_copy_channels", "mach_nn_adam",
               "mach_unet_create", "mach_unet_destroy", "mach_unet_get_info", "mach_unet_get_params",
@@ -68,6 +69,8 @@ def _L():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = C.c_int
+        L.mach_nn_debug_conv.argtypes = [i32, C.c_uint32]
+        L.mach_nn_debug_conv.restype = None
         _bound = True
     return L
 
@@ -121,6 +124,10 @@ def mach_nn_conv3d_tc(x, w_packed, co, bias, y, y_f32, flip=False, act=False, st
 
 def mach_nn_device_status(stream=None) -> int:
     return int(_L().mach_nn_device_status(_stream_ptr(stream)))
+
+
+def mach_nn_debug_conv(stall_copies: bool, wait_limit: int = 0) -> None:
+    _L().mach_nn_debug_conv(int(stall_copies), int(wait_limit))
 
 
 def mach_nn_conv3d_wgrad(x, dy, dw, stream=None):

@@ -408,3 +408,27 @@ def test_das_and_network_replay_from_one_cuda_graph():
             g.replay()
         torch.cuda.synchronize()
         assert torch.equal(out, eager)
+
+
+@pytest.mark.parametrize("ci,co", [(16, 16), (64, 128)])   # resident and streamed weights
+def test_tcgen05_bounded_waits_report_timeout_and_context_survives(ci, co):
+    nn = _nn()
+    r = np.random.default_rng(ci + co)
+    shape = (1, 4, 16, 16)
+    x, xh = _bf(r.standard_normal(shape + (ci,)))
+    w, wh = _bf(r.standard_normal((27, ci, co)) * 0.1)
+    wpk, _ = nn.mach_nn_pack_weights(w.float(), ci, co, flipped=False)
+    y = torch.empty(shape + (co,), dtype=torch.float32, device=dev)
+    assert nn.mach_nn_device_status() == 0
+    nn.mach_nn_debug_conv(True, 1 << 12)          # no copies are issued: every wait runs out
+    try:
+        nn.mach_nn_conv3d_tc(x, wpk, co, None, None, y)
+        assert nn.mach_nn_device_status() == 5     # MACH_ERR_TIMEOUT, reported once
+    finally:
+        nn.mach_nn_debug_conv(False, 0)
+    assert nn.mach_nn_device_status() == 0
+    nn.mach_nn_conv3d_tc(x, wpk, co, None, None, y)   # the same context computes correctly
+    assert nn.mach_nn_device_status() == 0
+    ref = U.conv3d(xh, wh)
+    bound = (27 * ci + 2) * 2.0 ** -24 * U.conv3d(np.abs(xh), np.abs(wh))
+    assert np.all(np.abs(y.cpu().double().numpy() - ref) <= bound)
