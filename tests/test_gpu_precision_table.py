@@ -1,0 +1,65 @@
+"""Error of every output (complex frames and Power Doppler) against the FP64 oracle on the
+unquantised complex64 data, for every workload and IQ storage type; prints the table and
+holds each entry to its gate (FP32 arithmetic throughout; 16-bit storage quantises the
+samples, the error bound derivations are in the parity tests)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import paper_2604_06257_gb300 as m
+from paper_2604_06257_gb300 import build as pkg_build
+
+pytestmark = pytest.mark.gpu
+
+GATES = {"c64": (-100.0, -60.0), "c64split": (-100.0, -60.0), "f16x2": (-60.0, -54.0), "bf16x2": (-50.0, -44.0)}
+ROWS = []
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pkg_build.build()
+    m.lib()
+    yield
+    print("\n| workload | IQ storage | frames NRMSE (dB) | Power Doppler NRMSE (dB) | voxels compared |")
+    print("|---|---|---|---|---|")
+    for r in ROWS:
+        print(f"| {r[0]} | {r[1]} | {r[2]:.1f} | {r[3]:.1f} | {r[4]} |")
+
+
+_DATA = {}
+
+
+def _workload(name):
+    if name not in _DATA:
+        _DATA.clear()
+        _DATA[name] = synth.make(name, "full", device="cuda")
+    return _DATA[name]
+
+
+def _db(a, b):
+    return 20 * np.log10(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("dt", ["c64", "c64split", "f16x2", "bf16x2"])
+@pytest.mark.parametrize("name", ["bmode2d", "doppler2d", "volume3d", "ulm3d"])
+def test_error_of_every_output(name, dt):
+    acq, iq = _workload(name)
+    if dt == "c64split" and (acq.n_frames % 4 or acq.n_frames <= 4):
+        pytest.skip("split rows need a frame count that is a multiple of 4 above 4")
+    a = acq.replace(iq_dtype=dt)
+    store = synth.iqmod.to_storage(iq, dt)
+    with m.Plan(**m.plan_kwargs(a)) as p:
+        pd, y = p.power_doppler(store, want_y=True)
+        torch.cuda.synchronize()
+    if acq.n_vox > 70000:
+        idx = np.sort(np.random.default_rng(11).choice(acq.n_vox, 256, replace=False))
+    else:
+        idx = np.arange(acq.n_vox)
+    y_ref, pd_ref = oracle.das(acq, iq.cpu(), idx)
+    e_y = _db(y.cpu().numpy()[idx].astype(np.complex128), y_ref)
+    e_pd = _db(pd.cpu().numpy()[idx].astype(np.float64), pd_ref)
+    ROWS.append((name, dt, e_y, e_pd, len(idx)))
+    gy, gpd = GATES[dt]
+    assert e_y <= gy and e_pd <= gpd, (e_y, e_pd)
