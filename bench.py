@@ -360,24 +360,40 @@ def run_ours(args):
                                       "variant": pi.info()["variant"]}
 
     # end to end through the public API with host buffers (pinned), copies timed: the host
-    # holds complex64 IQ in acquisition order; each step copies it in, converts it (K0),
-    # beamforms and copies the frames and Power Doppler out
+    # holds complex64 IQ in acquisition order; each step copies one acquisition in,
+    # converts it (K0), beamforms it and copies its frames and Power Doppler out.  The
+    # headline uses the native pipelined entry point (upload of k+1 overlapping the compute
+    # of k and the download of k-1) over a ring of distinct host buffers; the one-call-per-
+    # acquisition path, which serialises copies and compute, is reported beside it
     e2e = None
     if args.e2e_steps > 0:
-        iq_pin = iq_c64.permute(3, 0, 1, 2).contiguous().cpu().pin_memory()
-        pd_pin = torch.empty(V, dtype=torch.float32).pin_memory()
-        y_pin = torch.empty((V, F), dtype=torch.complex64).pin_memory()
-        for _ in range(3):
-            plan.power_doppler_host(iq_pin, pd_pin, y_pin, order="ftcs")
+        ring = 4
+        iq_host = iq_c64.permute(3, 0, 1, 2).contiguous().cpu()
+        iq_pin = [iq_host.clone().pin_memory() for _ in range(ring)]
+        pd_pin = [torch.empty(V, dtype=torch.float32).pin_memory() for _ in range(ring)]
+        y_pin = [torch.empty((V, F), dtype=torch.complex64).pin_memory() for _ in range(ring)]
+        K = args.e2e_steps
+        seq_iq = [iq_pin[k % ring] for k in range(K)]
+        seq_pd = [pd_pin[k % ring] for k in range(K)]
+        seq_y = [y_pin[k % ring] for k in range(K)]
+        plan.power_doppler_host_stream(seq_iq[:ring], seq_pd[:ring], seq_y[:ring], order="ftcs")
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            plan.power_doppler_host(iq_pin, pd_pin, y_pin, order="ftcs")
+        plan.power_doppler_host_stream(seq_iq, seq_pd, seq_y, order="ftcs")
         te = shard.max_over_ranks(time.perf_counter() - t0)
-        e2e = {"value": world * acq.points * args.e2e_steps / te, "unit": UNIT,
-               "h2d_bytes_per_step": iq_pin.numel() * iq_pin.element_size(),
-               "d2h_bytes_per_step": pd_pin.numel() * 4 + y_pin.numel() * 8,
-               "steps": args.e2e_steps}
+        for _ in range(3):
+            plan.power_doppler_host(iq_pin[0], pd_pin[0], y_pin[0], order="ftcs")
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            plan.power_doppler_host(iq_pin[0], pd_pin[0], y_pin[0], order="ftcs")
+        ts = shard.max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": world * acq.points * K / te, "unit": UNIT,
+               "h2d_bytes_per_step": iq_host.numel() * iq_host.element_size(),
+               "d2h_bytes_per_step": V * 4 + V * F * 8, "steps": K,
+               "api": "mach_power_doppler_host_stream (pipelined, 2 staging sets, 3 streams)",
+               "sequential": {"value": world * acq.points * K / ts, "unit": UNIT,
+                              "api": "mach_iq_convert + mach_power_doppler per call, synchronised"}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -133,6 +133,23 @@ mach_status mach_das_run(mach_plan p, const void *iq_dev, void *y_dev, void *str
 mach_status mach_power_doppler(mach_plan p, const void *iq_dev, float *pd_dev,
                                void *y_dev_or_null, void *stream);
 
+/* Power Doppler (Sec. 5) of `count` acquisitions held in HOST memory, pipelined: the
+ * upload of acquisition k+1 overlaps the conversion and beamforming of k and the download
+ * of k-1 (two device staging sets, separate upload / compute / download streams).
+ *   iq_host[k]   host IQ of acquisition k: complex64 in `src_order` (MACH_ORDER_*), which
+ *                K0 (mach_iq_convert) turns into the plan's layout on the device, or, with
+ *                src_order = -1, already in the plan's layout and iq_dtype;
+ *   pd_host[k]   host float32 [n_vox] receiving its Power Doppler;
+ *   y_host       NULL, or y_host[k] = host complex64 [n_vox][n_frames] for its frames.
+ * Host buffers should be pinned (page-locked) for the copies to overlap; the caller keeps
+ * ownership.  Staging buffers and streams are allocated for the call and released before
+ * it returns; the call returns when every result is in host memory.  Results are bitwise
+ * those of mach_iq_convert + mach_power_doppler on each acquisition.
+ * Errors: INVALID_ARG (NULL plan or pointer, count < 1, bad order), OOM, CUDA, and
+ * TIMEOUT (the plan's device status, read and cleared after the last acquisition). */
+mach_status mach_power_doppler_host_stream(mach_plan p, const void *const *iq_host, int32_t src_order,
+                                           float *const *pd_host, void *const *y_host, int32_t count);
+
 /* Channel-data preparation (K0): read complex64 IQ in `src_order` and write it in the
  * frame-contiguous layout [n_tx][n_elem][n_samples][n_frames] (Sec. 4.4's element,
  * sample, frame order with the transmit axis in front) as `dst_dtype` (float16 and

@@ -33,7 +33,7 @@ EXPORTS = ("mach_das_plan", "mach_das_run", "mach_power_doppler", "mach_plan_des
            "mach_debug_force_variant", "mach_debug_set_wait_limit", "mach_debug_stall_producer",
            "mach_das_run_noalloc", "mach_iq_convert", "mach_batch_plan", "mach_batch_bind",
            "mach_batch_run", "mach_batch_get_info", "mach_batch_destroy", "mach_das_run_per_tx",
-           "mach_rf_to_iq")
+           "mach_rf_to_iq", "mach_power_doppler_host_stream")
 
 
 class MachError(RuntimeError):
@@ -101,6 +101,8 @@ def lib():
         L.mach_rf_to_iq.restype = C.c_int
         L.mach_das_run_per_tx.restype = C.c_int
         L.mach_power_doppler.argtypes = [vp, vp, vp, vp, vp]
+        L.mach_power_doppler_host_stream.argtypes = [vp, C.POINTER(vp), i32, C.POINTER(vp), C.POINTER(vp), i32]
+        L.mach_power_doppler_host_stream.restype = C.c_int
         L.mach_plan_destroy.argtypes = [vp]
         L.mach_status_string.argtypes = [C.c_int]
         L.mach_status_string.restype = C.c_char_p
@@ -276,6 +278,32 @@ def mach_power_doppler(plan: int, iq, pd, y=None, stream=None) -> None:
                                   _stream_ptr(stream))
     if st != MACH_OK:
         raise MachError(st, "mach_power_doppler")
+
+
+def _host_ptr(t, what):
+    """Address of a contiguous CPU tensor."""
+    if t.is_cuda:
+        raise ValueError(f"{what} must be a host tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return t.data_ptr()
+
+
+def mach_power_doppler_host_stream(plan: int, iq_host, src_order, pd_host, y_host=None) -> None:
+    """Pipelined Power Doppler of acquisitions in host memory (lists of CPU tensors, pinned
+    for overlap): src_order "ftcs" / "tcsf" (complex64, converted by K0 on the device) or
+    None (already in the plan's layout and storage type)."""
+    n = len(iq_host)
+    if len(pd_host) != n or (y_host is not None and len(y_host) != n):
+        raise ValueError("iq_host, pd_host and y_host must have the same length")
+    arr = C.c_void_p * max(n, 1)
+    iq_a = arr(*[_host_ptr(t, "iq_host") for t in iq_host])
+    pd_a = arr(*[_host_ptr(t, "pd_host") for t in pd_host])
+    y_a = arr(*[_host_ptr(t, "y_host") for t in y_host]) if y_host is not None else None
+    order = -1 if src_order is None else ORDER.get(src_order, src_order)
+    st = lib().mach_power_doppler_host_stream(plan, iq_a, order, pd_a, y_a, n)
+    if st != MACH_OK:
+        raise MachError(st, "mach_power_doppler_host_stream")
 
 
 def mach_das_run_noalloc(desc, iq, y=None, pd=None, stream=None) -> None:
@@ -501,6 +529,28 @@ class Plan:
             if y_host is not None:
                 y_host.copy_(y_d, non_blocking=True)
         s.synchronize()
+        return pd_host, y_host
+
+    def power_doppler_host_stream(self, iq_host, pd_host, y_host=None, order=None):
+        """Power Doppler of several acquisitions in host memory, pipelined in native code
+        (mach.h: mach_power_doppler_host_stream): lists of host tensors shaped as for
+        ``power_doppler_host``; returns when every result is in host memory."""
+        if order is None:
+            for t in iq_host:
+                self._check_iq(t)
+        else:
+            T, Cn, S, F = self.iq_shape
+            want = (F, T, Cn, S) if order == "ftcs" else (T, Cn, S, F)
+            for t in iq_host:
+                if tuple(t.shape) != want or t.dtype != self._torch.complex64:
+                    raise ValueError(f"iq_host must be complex64 {want}")
+        for t in pd_host:
+            if t.numel() != self.n_vox or t.dtype != self._torch.float32:
+                raise ValueError("pd_host must be float32 [n_vox]")
+        for t in (y_host or []):
+            if t.numel() != self.n_vox * self.n_frames or t.dtype != self._torch.complex64:
+                raise ValueError("y_host must be complex64 [n_vox, n_frames]")
+        mach_power_doppler_host_stream(self.handle, iq_host, order, pd_host, y_host)
         return pd_host, y_host
 
     def tx_table(self):

@@ -144,6 +144,7 @@ int batch_blocks_per_sm(int iq_dtype);
 cudaError_t launch_batch(int iq_dtype, const BatchInstance* insts, const int2* items, int n_items, int* counter,
                          int grid, cudaStream_t s);
 const DasParams* plan_params(mach_plan p);
+int plan_iq_dtype(mach_plan p);
 void pick_tile_shape(int n, int nx, int ny, int nz, bool list, int tile[3]);
 
 // Host steps shared by mach_das_plan and the allocation-free entry point.

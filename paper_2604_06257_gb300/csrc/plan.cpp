@@ -647,5 +647,6 @@ uint32_t host_fixed_cycles(double cycles) { return fixed_cycles(cycles); }
 
 namespace mach {
 const DasParams* plan_params(mach_plan p) { return p ? &p->base : nullptr; }
+int plan_iq_dtype(mach_plan p) { return p ? p->d.iq_dtype : -1; }
 void pick_tile_shape(int n, int nx, int ny, int nz, bool list, int tile[3]) { pick_tile(n, nx, ny, nz, list, tile); }
 }  // namespace mach

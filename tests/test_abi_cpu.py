@@ -97,6 +97,7 @@ def test_null_arguments():
     assert L.mach_das_plan(C.byref(d), None, None) == m.MACH_ERR_INVALID_ARG
     assert L.mach_das_run(None, None, None, None) == m.MACH_ERR_INVALID_ARG
     assert L.mach_power_doppler(None, None, None, None, None) == m.MACH_ERR_INVALID_ARG
+    assert L.mach_power_doppler_host_stream(None, None, 0, None, None, 1) == m.MACH_ERR_INVALID_ARG
     assert L.mach_plan_destroy(None) == m.MACH_OK
     assert L.mach_plan_get_info(None, None) == m.MACH_ERR_INVALID_ARG
     assert L.mach_plan_tx_table(None, None, None) == m.MACH_ERR_INVALID_ARG
