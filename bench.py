@@ -358,6 +358,35 @@ def run_ours(args):
             tt = statistics.mean(a.elapsed_time(b) for a, b in ts) / 1e3
             alt["c64_interleaved"] = {"value": acq.points / tt, "ms_per_step": tt * 1e3,
                                       "variant": pi.info()["variant"]}
+        # the same step reading every term from a plan-time table (mach_das_desc.term_table)
+        # instead of evaluating it, and its check against the on-the-fly result
+        try:
+            pt = m.Plan(**m.plan_kwargs(acq), term_table=True)
+        except m.MachError as e:
+            alt["term_table"] = {"unavailable": str(e)}
+        else:
+            with pt:
+                pd_t = torch.empty_like(pd)
+                y_t = torch.empty_like(y)
+                for _ in range(args.warmup):
+                    flush.zero_()
+                    m.mach_power_doppler(pt.handle, iq, pd_t, y_t)
+                ts = []
+                for _ in range(min(args.steps, 1000)):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    m.mach_power_doppler(pt.handle, iq, pd_t, y_t)
+                    e1.record(stream)
+                    ts.append((e0, e1))
+                torch.cuda.synchronize()
+                tt = statistics.mean(a.elapsed_time(b) for a, b in ts) / 1e3
+                m.mach_power_doppler(plan.handle, iq, pd, y)
+                torch.cuda.synchronize()
+                ti = pt.info()
+                alt["term_table"] = {"value": acq.points / tt, "ms_per_step": tt * 1e3, "variant": ti["variant"],
+                                     "table_bytes": ti["term_table_bytes"],
+                                     "bitwise_equal_to_on_the_fly": bool(torch.equal(y_t, y) and torch.equal(pd_t, pd))}
 
     # end to end through the public API with host buffers (pinned), copies timed: the host
     # holds complex64 IQ in acquisition order; each step copies one acquisition in,

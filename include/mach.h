@@ -108,12 +108,24 @@ typedef struct {
     int32_t n_samples;           /* samples per channel, 2 .. 2^24                       */
     int32_t n_frames;            /* frames (ensemble), >= 1                              */
     int32_t iq_dtype;            /* mach_iq_dtype                                        */
+    int32_t term_table;          /* 0: receive delays, indices, weights and phases are
+                                    computed in every run (Sec. 4.3's hybrid delays);
+                                    1: the plan evaluates every term once and stores it
+                                    (16 bytes per voxel slot and usable element-transmit
+                                    pair of each voxel tile; mach_plan_info.
+                                    term_table_bytes) and runs read the table instead.
+                                    Same outputs bit for bit.  Plans only: the batch and
+                                    allocation-free entry points need 0               */
 } mach_das_desc;
 
 /* Build a plan (Sec. 4.3 precompute): validates `d`, copies its host arrays, allocates
  * the device tables (voxel coordinates in sample units, element coordinates, the
  * transmit delay table [n_tx][n_vox] float32 built in FP64 on the device) and selects
  * the kernel variant.  Runs on `stream` and synchronises it before returning.
+ * With term_table = 1 it also evaluates and stores every term (see mach_das_desc);
+ * UNSUPPORTED when the selected kernel has no table form (ensembles of 16 frames or
+ * fewer, or above 64, or sample windows too long for shared memory), OOM when the table
+ * does not fit in free device memory.
  * Errors: INVALID_ARG (checked before any CUDA call), OOM, CUDA, UNSUPPORTED.
  * On error *out is set to NULL and nothing is leaked. */
 mach_status mach_das_plan(const mach_das_desc *d, void *stream, mach_plan *out);
@@ -208,6 +220,7 @@ typedef struct {
     int32_t ring_slots;      /* staged variants: slots in the ring (0 otherwise)        */
     int64_t copy_pairs;      /* staged variants: (tile, transmit, element) windows one
                                 run copies; pairs no voxel can use are skipped          */
+    int64_t term_table_bytes; /* device bytes of the term table (0 without one)         */
 } mach_plan_info;
 
 mach_status mach_plan_get_info(mach_plan p, mach_plan_info *info);

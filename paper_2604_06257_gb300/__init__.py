@@ -50,7 +50,7 @@ class mach_das_desc(C.Structure):
         ("n_tx", C.c_int32), ("tx_angles", C.c_void_p), ("tx_table_dev", C.c_void_p),
         ("fs", C.c_double), ("fc", C.c_double), ("c", C.c_double), ("t0", C.c_double),
         ("f_number", C.c_double), ("apod", C.c_int32), ("n_samples", C.c_int32),
-        ("n_frames", C.c_int32), ("iq_dtype", C.c_int32),
+        ("n_frames", C.c_int32), ("iq_dtype", C.c_int32), ("term_table", C.c_int32),
     ]
 
 
@@ -60,7 +60,7 @@ class mach_plan_info(C.Structure):
         ("voxels_per_cta", C.c_int32), ("threads_per_cta", C.c_int32), ("tile", C.c_int32 * 3),
         ("frame_tiles", C.c_int32), ("ctas", C.c_int64), ("smem_bytes", C.c_int64),
         ("device_bytes", C.c_int64), ("ring_rows", C.c_int32), ("ring_slots", C.c_int32),
-        ("copy_pairs", C.c_int64),
+        ("copy_pairs", C.c_int64), ("term_table_bytes", C.c_int64),
     ]
 
     def as_dict(self):
@@ -69,7 +69,8 @@ class mach_plan_info(C.Structure):
                 "threads_per_cta": self.threads_per_cta, "tile": list(self.tile),
                 "frame_tiles": self.frame_tiles, "ctas": self.ctas, "smem_bytes": self.smem_bytes,
                 "device_bytes": self.device_bytes, "ring_rows": self.ring_rows,
-                "ring_slots": self.ring_slots, "copy_pairs": self.copy_pairs}
+                "ring_slots": self.ring_slots, "copy_pairs": self.copy_pairs,
+                "term_table_bytes": self.term_table_bytes}
 
 
 class mach_tile_shape(C.Structure):
@@ -219,8 +220,9 @@ def make_desc(*, ndim: int, elem_pos, fs: float, fc: float, c: float, n_samples:
               n_frames: int, tx_angles=None, tx_table_dev=None, t0: float = 0.0,
               f_number: float = 1.0, apod: str = "boxcar", vox_pos=None,
               grid_dims: Optional[Sequence[int]] = None, grid_origin=(0.0, 0.0, 0.0),
-              grid_step=(0.0, 0.0, 0.0), iq_dtype: str = "c64"):
-    """Build a ``mach_das_desc`` (plus the host arrays it references)."""
+              grid_step=(0.0, 0.0, 0.0), iq_dtype: str = "c64", term_table: bool = False):
+    """Build a ``mach_das_desc`` (plus the host arrays it references).  ``term_table``:
+    the plan stores every term instead of computing them per run (mach.h)."""
     h = _HostArrays()
     d = mach_das_desc()
     d.ndim = ndim
@@ -248,6 +250,7 @@ def make_desc(*, ndim: int, elem_pos, fs: float, fc: float, c: float, n_samples:
     d.apod = APOD[apod] if isinstance(apod, str) else int(apod)
     d.n_samples, d.n_frames = n_samples, n_frames
     d.iq_dtype = IQ_DTYPE[iq_dtype] if isinstance(iq_dtype, str) else int(iq_dtype)
+    d.term_table = int(term_table)
     return d, h
 
 

@@ -70,6 +70,7 @@ mach_status mach_batch_plan(const mach_das_desc* descs, int32_t n, const mach_ti
   for (int i = 0; i < n; ++i) {
     mach_status st = host_validate(&descs[i]);
     if (st != MACH_OK) return st;
+    if (descs[i].term_table) return MACH_ERR_UNSUPPORTED;
     if (descs[i].iq_dtype != dt) return MACH_ERR_INVALID_ARG;
     if (descs[i].n_frames > 64) return MACH_ERR_UNSUPPORTED;
     if (shapes) {

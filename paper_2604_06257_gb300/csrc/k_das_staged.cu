@@ -1,28 +1,13 @@
-// k_das_staged.cu -- delay-and-sum with the sample windows staged in shared memory.
-//
-// One block beamforms a compact tile of voxels for all frames of the frame tile.  For
-// every (element, transmit) pair that some voxel of the tile can use, the rows of the
-// frame-contiguous IQ slab that the tile can touch form ONE contiguous byte range
-// (rows lo .. lo+rows-1, all F frames), so a single bulk asynchronous copy (TMA unit)
-// brings the window into a ring slot of shared memory.  A producer warp walks the
-// pairs, issues the copies and publishes each slot's (transmit, element, lo, rows);
-// the consumer warps evaluate their terms (receive delay, index, weight) once per pair
-// and reuse them across all frames (Sec. 4.4's delay reuse), reading both taps of every
-// frame from shared memory.  Pairs no voxel of the tile can use (outside every voxel's
-// aperture, or out of range) are skipped without a copy.
-//
-// Synchronisation: per slot a "full" mbarrier (producer arrival + transaction bytes)
-// and an "empty" mbarrier (one arrival per consumer warp).  Every wait is bounded; on a
-// timeout the kernel sets bit 0 of the plan's error word and returns.
+// k_das_staged.cu -- the staged delay-and-sum kernel with terms evaluated on the fly
+// (Sec. 4.3's hybrid delays), and the plan-time bounds every staged variant needs (per
+// tile: voxel bounding box and transmit-delay range, from which each (element,
+// transmit) pair's sample window follows).  The kernel itself is in das_staged.cuh.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
-#include "async_copy.cuh"
-#include "das_term.cuh"
-#include "tap_mac.cuh"
-#include "mach_internal.h"
+#include "das_staged.cuh"
 
 namespace mach {
 
@@ -117,321 +102,33 @@ cudaError_t launch_tile_bounds(const DasParams& p, float4* tbox, float2* txr, in
   return cudaGetLastError();
 }
 
-// ---- the staged kernel --------------------------------------------------------------------
-constexpr int kTxCache = 16;   // transmits whose delays are cached in shared memory per warp
-
-// Shared memory: [ring slots][term tables][transmit-delay cache][slot metadata][barriers]
-template <int NBUF>
-struct RingLayout {
-  size_t slot_bytes, tx_bytes;
-  __host__ __device__ RingLayout(int rows_cap, int F, int iq_bytes, int T, int nwc)
-      : slot_bytes(((static_cast<size_t>(rows_cap) * F * iq_bytes) + 127) / 128 * 128),
-        tx_bytes(T <= kTxCache ? static_cast<size_t>(nwc) * T * 32 * 4 : 0) {}
-  __host__ __device__ size_t terms_off() const { return NBUF * slot_bytes; }
-  __host__ __device__ size_t tx_off(int nwc) const { return terms_off() + static_cast<size_t>(nwc) * 32 * 16; }
-  __host__ __device__ size_t meta_off(int nwc) const { return tx_off(nwc) + (tx_bytes + 15) / 16 * 16; }
-  __host__ __device__ size_t bar_off(int nwc) const { return meta_off(nwc) + NBUF * 32; }
-  __host__ __device__ size_t total(int nwc) const { return bar_off(nwc) + 2 * NBUF * 8; }
-};
-
-// Slot metadata published by the producer with each window.
-struct SlotMeta {
-  int t, c, lo, rows;   // c < 0: end of sequence
-  float4 e;             // element position (sample units)
-};
-
-// MAXR: register cap per thread, chosen so that the intended number of blocks fits per SM
-template <class IQ, int VEC, int NV, int FL, int VPG, int NWC, int NBUF, int MAXR>
-__global__ void __launch_bounds__((NWC + 1) * 32) __maxnreg__(MAXR) k_das_staged(const DasParams p) {
-  constexpr int G = 32 / FL;
-  constexpr int WV = G * VPG;
-  constexpr int FPL = VEC * NV;
-  constexpr int FT = FL * FPL;
-  constexpr int PB = 32 / WV;          // pairs whose terms one warp evaluates per round
-  static_assert(WV * PB == 32, "a round must fill the warp");
-  static_assert(NBUF >= PB, "a round must fit in the ring");
-  extern __shared__ __align__(128) unsigned char smem[];
-  using E = typename IqStore<IQ>::E;
-  constexpr int kBytes = static_cast<int>(sizeof(E)) * IqStore<IQ>::eps;   // bytes per complex sample
-  const RingLayout<NBUF> L(p.rows_cap, p.F, kBytes, p.T, NWC);
-  E* ring = reinterpret_cast<E*>(smem);
-  float4* terms_all = reinterpret_cast<float4*>(smem + L.terms_off());
-  float* txc_all = reinterpret_cast<float*>(smem + L.tx_off(NWC));
-  SlotMeta* meta = reinterpret_cast<SlotMeta*>(smem + L.meta_off(NWC));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bar_off(NWC));
-  uint64_t* empty = full + NBUF;
-  const size_t slot_elems = L.slot_bytes / sizeof(E);
-  const int row_elems = p.F * IqStore<IQ>::eps;     // one sample row, all frames
-  const bool tx_cached = p.T <= kTxCache;
-
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const int64_t tile = blockIdx.x;
-  const E* __restrict__ iq = static_cast<const E*>(p.iq);
-  const size_t slab = static_cast<size_t>(p.S) * row_elems;
-
-  if (threadIdx.x == 0) {
-    for (int b = 0; b < NBUF; ++b) {
-      mbar_init(&full[b], 1);
-      mbar_init(&empty[b], NWC);
-    }
-    mbar_init_fence();
-  }
-  __syncthreads();
-
-  // ------------------------------------------------------------------ producer
-  // The producer warp evaluates 32 (element, transmit) pairs at a time (one lane each,
-  // loads issued together), then lane 0 issues the copies of the usable ones in order.
-  if (warp == NWC) {
-    const float4 blo = p.tbox[2 * tile], bhi = p.tbox[2 * tile + 1];
-    const int npairs = p.C * p.T;
-    int r = 0;
-    bool ok = true;
-    for (int pb = 0; pb < npairs && ok; pb += 32) {
-      const int pi = pb + lane;
-      int t = 0, c = 0, lo = 0, rows = 0;
-      float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
-      bool use = false;
-      if (pi < npairs) {
-        c = pi / p.T;
-        t = pi - c * p.T;
-        e = __ldg(&p.elem[c]);
-        use = pair_window(blo, bhi, __ldg(&p.txr[tile * p.txr_stride + t]), e, p, lo, rows);
-        rows = min(rows, p.rows_cap);
-      }
-      unsigned todo = __ballot_sync(0xffffffffu, use);
-      while (todo) {
-        const int j = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const int tj = __shfl_sync(0xffffffffu, t, j), cj = __shfl_sync(0xffffffffu, c, j);
-        const int loj = __shfl_sync(0xffffffffu, lo, j), rowsj = __shfl_sync(0xffffffffu, rows, j);
-        float4 ej;
-        ej.x = __shfl_sync(0xffffffffu, e.x, j);
-        ej.y = __shfl_sync(0xffffffffu, e.y, j);
-        ej.z = __shfl_sync(0xffffffffu, e.z, j);
-        ej.w = 0.f;
-        if (lane == 0) {
-          const int slot = r % NBUF;
-          if (r >= NBUF && !mbar_wait_bounded(&empty[slot], ((r / NBUF) - 1) & 1, p.wait_limit)) {
-            atomicOr(p.err, 1);
-            ok = false;
-          } else {
-            meta[slot].t = tj;
-            meta[slot].c = cj;
-            meta[slot].lo = loj;
-            meta[slot].rows = rowsj;
-            meta[slot].e = ej;
-            const uint32_t bytes = static_cast<uint32_t>(rowsj) * p.F * kBytes;
-            mbar_arrive_expect_tx(&full[slot], bytes);
-            if (!p.debug_stall)
-              bulk_g2s(ring + slot * slot_elems,
-                       iq + (static_cast<size_t>(tj) * p.C + cj) * slab + static_cast<size_t>(loj) * row_elems, bytes,
-                       &full[slot]);
-          }
-        }
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) break;
-        ++r;
-      }
-    }
-    if (lane != 0) return;
-    if (ok) {   // one end-of-sequence marker per pair a consumer round can hold
-      for (int k = 0; k < PB; ++k) {
-        const int rr = r + k, slot = rr % NBUF;
-        if (rr >= NBUF && !mbar_wait_bounded(&empty[slot], ((rr / NBUF) - 1) & 1, p.wait_limit)) {
-          atomicOr(p.err, 1);
-          break;
-        }
-        meta[slot].c = -1;
-        mbar_arrive(&full[slot]);
-      }
-    } else {    // abandoning: let the copies already issued land before the block can exit
-      for (int k = max(0, r - NBUF); k < r; ++k) mbar_wait_bounded(&full[k % NBUF], (k / NBUF) & 1, p.wait_limit);
-    }
-    return;
-  }
-
-  // ------------------------------------------------------------------ consumers
-  // Each round the warp takes PB consecutive pairs: lane group `sub` (WV lanes) evaluates
-  // the terms of pair r + sub for the warp's WV voxels, then the warp consumes the PB
-  // pairs one after the other.
-  const int g = lane / FL;
-  const int jl = lane % FL;
-  const int sub = lane / WV;
-  const int q = lane % WV;
-  const int f_base = blockIdx.y * FT;
-  float4* terms = terms_all + warp * 32;
-  float* txc = txc_all + warp * (p.T * 32);
-  // terms of voxel slot q for pair `sub` are stored at sub*WV + k*G + g (slot q = g*VPG + k),
-  // so the G groups of the warp read G consecutive entries (no bank conflict)
-  const int64_t v_term = tile_voxel_blocked(p, tile, warp * WV + q);
-  const float4 vpos = v_term >= 0 ? p.vox[v_term] : make_float4(0.f, 0.f, 0.f, 0.f);
-  const int store_at = sub * WV + (q % VPG) * G + (q / VPG);
-  if (tx_cached) {
-    for (int t = 0; t < p.T; ++t) txc[t * 32 + lane] = v_term >= 0 ? p.tx[static_cast<size_t>(t) * p.V + v_term] : 0.f;
-  }
-
-  float2 acc[VPG][FPL];
-#pragma unroll
-  for (int k = 0; k < VPG; ++k)
-#pragma unroll
-    for (int e = 0; e < FPL; ++e) acc[k][e] = make_float2(0.f, 0.f);
-
-  int cur_c = -1;
-  TermGeo geo;
-  geo.rx = 0.f;
-  geo.a = -1.f;
-  bool ok = true, done = false;
-  for (int r = 0; !done; r += PB) {
-    const int mine = r + sub, my_slot = mine % NBUF;
-    const bool got = mbar_wait_bounded(&full[my_slot], (mine / NBUF) & 1, p.wait_limit);
-    if (__any_sync(0xffffffffu, !got)) {
-      if (lane == 0) atomicOr(p.err, 1);
-      ok = false;
-      break;
-    }
-    const SlotMeta mm = meta[my_slot];
-    float4 rec = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
-    if (mm.c >= 0) {
-      if (mm.c != cur_c) {
-        cur_c = mm.c;
-        geo.a = -1.f;
-        if (v_term >= 0) geo = term_geometry(vpos, mm.e, p);
-      }
-      if (geo.a >= 0.f) {
-        const float stx = tx_cached ? txc[mm.t * 32 + lane] : __ldg(&p.tx[static_cast<size_t>(mm.t) * p.V + v_term]);
-        rec = term_record(stx, geo, p);
-      }
-    }
-    const int my_i0 = __float_as_int(rec.w);
-    const bool active = my_i0 >= 0;
-    const bool outside = active && (my_i0 - mm.lo < 0 || my_i0 - mm.lo + 1 >= mm.rows);
-    const unsigned act = __ballot_sync(0xffffffffu, active);
-    const unsigned outm = __ballot_sync(0xffffffffu, outside);
-    const unsigned ended = __ballot_sync(0xffffffffu, mm.c < 0);
-    terms[store_at] = rec;
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < PB; ++i) {
-      const unsigned gm = WV == 32 ? 0xffffffffu : (((1u << (WV & 31)) - 1u) << (i * WV));
-      if (ended & gm) {   // end marker: every later pair of the round is one too
-        done = true;
-        break;
-      }
-      if (!(act & gm)) continue;
-      const int slot = (r + i) % NBUF;
-      const int lo = meta[slot].lo, rows = meta[slot].rows;
-      const E* win = ring + slot * slot_elems;
-      const float4* tp = terms + i * WV;
-      if (!(outm & gm)) {
-        // every kept term lies in the staged window: branch-free over the voxels
-        // (dropped terms carry zero weights and read row 0)
-#pragma unroll
-        for (int k = 0; k < VPG; ++k) {
-          const float4 tr = tp[k * G + g];
-          const int row = max(__float_as_int(tr.w) - lo, 0);
-          const float c1r = tr.x * tr.z, c1i = tr.y * tr.z;
-          const float c0r = tr.x - c1r, c0i = tr.y - c1i;
-          gather_mac<IQ, VEC, NV, FL, true>(acc[k], win + row * row_elems, row_elems, p.F, f_base, jl, c0r, c0i, c1r,
-                                            c1i);
-        }
-      } else {
-        // some kept term falls outside the staged window (not expected): per-term
-        // choice between the window and global memory
-        const int t = meta[slot].t, c = meta[slot].c;
-        const E* gsrc = iq + (static_cast<size_t>(t) * p.C + c) * slab;
-#pragma unroll
-        for (int k = 0; k < VPG; ++k) {
-          const float4 tr = tp[k * G + g];
-          const int i0 = __float_as_int(tr.w);
-          if (i0 >= 0) {
-            const float c1r = tr.x * tr.z, c1i = tr.y * tr.z;
-            const float c0r = tr.x - c1r, c0i = tr.y - c1i;
-            const int row = i0 - lo;
-            if (row >= 0 && row + 1 < rows)
-              gather_mac<IQ, VEC, NV, FL, true>(acc[k], win + row * row_elems, row_elems, p.F, f_base, jl, c0r, c0i,
-                                                c1r, c1i);
-            else
-              gather_mac<IQ, VEC, NV, FL, false>(acc[k], gsrc + static_cast<size_t>(i0) * row_elems, row_elems, p.F,
-                                                 f_base, jl, c0r, c0i, c1r, c1i);
-          }
-        }
-      }
-    }
-    __syncwarp();
-    if (lane < PB) mbar_arrive(&empty[(r + lane) % NBUF]);
-  }
-  if (!ok) return;
-
-#pragma unroll
-  for (int k = 0; k < VPG; ++k) {
-    const int64_t v = tile_voxel_blocked(p, tile, warp * WV + g * VPG + k);
-    float pw = 0.f;
-#pragma unroll
-    for (int mm = 0; mm < NV; ++mm) {
-      const int f = f_base + (jl + FL * mm) * VEC;
-      if (f < p.F) {
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-          const float2 a = acc_frame<IQ, VEC>(&acc[k][mm * VEC], e);
-          pw = fmaf(a.x, a.x, fmaf(a.y, a.y, pw));
-        }
-        if (v >= 0 && p.y) {
-          float2* dst = p.y + v * p.ystride + f;
-#pragma unroll
-          for (int e = 0; e < VEC; e += 2) {
-            const float2 a = acc_frame<IQ, VEC>(&acc[k][mm * VEC], e), b = acc_frame<IQ, VEC>(&acc[k][mm * VEC], e + 1);
-            *reinterpret_cast<float4*>(dst + e) = make_float4(a.x, a.y, b.x, b.y);
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int o = FL / 2; o > 0; o >>= 1) pw += __shfl_xor_sync(0xffffffffu, pw, o);
-    if (jl == 0 && v >= 0 && p.pd) p.pd[v] = pw;
-  }
-}
-
 // ---- dispatch ------------------------------------------------------------------------------
-namespace {
-constexpr int kRing = 4;    // ring slots (8 when a round holds 4 pairs)
-
-template <class K>
-cudaError_t go_staged(K kernel, int nwc, const DasParams& p, size_t smem, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (e != cudaSuccess) return e;
-  const int64_t tiles = static_cast<int64_t>(p.tiles_x) * p.tiles_y * p.tiles_z;
-  kernel<<<dim3(static_cast<unsigned>(tiles), 1), (nwc + 1) * 32, smem, s>>>(p);
-  return cudaGetLastError();
-}
-}  // namespace
-
-size_t staged_smem_bytes(Variant v, int rows_cap, int F, int T) {
+size_t staged_smem_bytes(Variant v, int rows_cap, int F, int T, bool table) {
   const VariantShape& sh = variant_shape(v);
-  if (sh.ring_slots == 8) return RingLayout<8>(rows_cap, F, sh.iq_bytes, T, sh.warps).total(sh.warps);
-  return RingLayout<kRing>(rows_cap, F, sh.iq_bytes, T, sh.warps).total(sh.warps);
+  if (sh.ring_slots == 8) return RingLayout<8>(rows_cap, F, sh.iq_bytes, T, sh.warps, sh.voxels_per_warp, table).total();
+  return RingLayout<kRing>(rows_cap, F, sh.iq_bytes, T, sh.warps, sh.voxels_per_warp, table).total();
 }
 
 cudaError_t launch_das_staged(const DasParams& p, Variant v, cudaStream_t s) {
-  const size_t sm = staged_smem_bytes(v, p.rows_cap, p.F, p.T);
+  const size_t sm = staged_smem_bytes(v, p.rows_cap, p.F, p.T, false);
   switch (v) {
-    case V_ST32_C64: return go_staged(k_das_staged<float2, 2, 2, 8, 8, 8, kRing, 112>, 8, p, sm, s);
-    case V_ST64_C64: return go_staged(k_das_staged<float2, 2, 2, 16, 8, 8, kRing, 112>, 8, p, sm, s);
-    case V_ST32_H16: return go_staged(k_das_staged<__half2, 4, 1, 8, 8, 8, kRing, 112>, 8, p, sm, s);
-    case V_ST64_H16: return go_staged(k_das_staged<__half2, 4, 1, 16, 8, 8, kRing, 112>, 8, p, sm, s);
-    case V_ST32_C64_V4: return go_staged(k_das_staged<float2, 2, 2, 8, 4, 8, kRing, 72>, 8, p, sm, s);
-    case V_ST32_C64_V4W4: return go_staged(k_das_staged<float2, 2, 2, 8, 4, 4, kRing, 80>, 4, p, sm, s);
-    case V_ST32_C64_V4R56: return go_staged(k_das_staged<float2, 2, 2, 8, 4, 8, kRing, 56>, 8, p, sm, s);
-    case V_ST32_C64P_V4: return go_staged(k_das_staged<C64Planar, 4, 1, 8, 4, 8, kRing, 72>, 8, p, sm, s);
-    case V_ST64_C64P_V4: return go_staged(k_das_staged<C64Planar, 4, 1, 16, 4, 8, 8, 72>, 8, p, sm, s);
-    case V_ST32_C64P_V4W7: return go_staged(k_das_staged<C64Planar, 4, 1, 8, 4, 7, kRing, 64>, 7, p, sm, s);
-    case V_ST32_C64_V4W7: return go_staged(k_das_staged<float2, 2, 2, 8, 4, 7, kRing, 64>, 7, p, sm, s);
-    case V_ST32_H16_V4: return go_staged(k_das_staged<__half2, 4, 1, 8, 4, 8, kRing, 72>, 8, p, sm, s);
-    case V_ST32_B16_V4: return go_staged(k_das_staged<__nv_bfloat162, 4, 1, 8, 4, 8, kRing, 72>, 8, p, sm, s);
-    case V_ST64_C64_V4: return go_staged(k_das_staged<float2, 2, 2, 16, 4, 8, 8, 72>, 8, p, sm, s);
-    case V_ST64_H16_V4: return go_staged(k_das_staged<__half2, 4, 1, 16, 4, 8, 8, 72>, 8, p, sm, s);
-    case V_ST32_B16: return go_staged(k_das_staged<__nv_bfloat162, 4, 1, 8, 8, 8, kRing, 112>, 8, p, sm, s);
-    case V_ST64_B16_V4: return go_staged(k_das_staged<__nv_bfloat162, 4, 1, 16, 4, 8, 8, 72>, 8, p, sm, s);
+    case V_ST32_C64: return go_staged(k_das_staged<float2, 2, 2, 8, 8, 8, kRing, 112, false>, 8, p, sm, s);
+    case V_ST64_C64: return go_staged(k_das_staged<float2, 2, 2, 16, 8, 8, kRing, 112, false>, 8, p, sm, s);
+    case V_ST32_H16: return go_staged(k_das_staged<__half2, 4, 1, 8, 8, 8, kRing, 112, false>, 8, p, sm, s);
+    case V_ST64_H16: return go_staged(k_das_staged<__half2, 4, 1, 16, 8, 8, kRing, 112, false>, 8, p, sm, s);
+    case V_ST32_C64_V4: return go_staged(k_das_staged<float2, 2, 2, 8, 4, 8, kRing, 72, false>, 8, p, sm, s);
+    case V_ST32_C64_V4W4: return go_staged(k_das_staged<float2, 2, 2, 8, 4, 4, kRing, 80, false>, 4, p, sm, s);
+    case V_ST32_C64_V4R56: return go_staged(k_das_staged<float2, 2, 2, 8, 4, 8, kRing, 56, false>, 8, p, sm, s);
+    case V_ST32_C64P_V4: return go_staged(k_das_staged<C64Planar, 4, 1, 8, 4, 8, kRing, 72, false>, 8, p, sm, s);
+    case V_ST64_C64P_V4: return go_staged(k_das_staged<C64Planar, 4, 1, 16, 4, 8, 8, 72, false>, 8, p, sm, s);
+    case V_ST32_C64P_V4W7: return go_staged(k_das_staged<C64Planar, 4, 1, 8, 4, 7, kRing, 64, false>, 7, p, sm, s);
+    case V_ST32_C64_V4W7: return go_staged(k_das_staged<float2, 2, 2, 8, 4, 7, kRing, 64, false>, 7, p, sm, s);
+    case V_ST32_H16_V4: return go_staged(k_das_staged<__half2, 4, 1, 8, 4, 8, kRing, 72, false>, 8, p, sm, s);
+    case V_ST32_B16_V4: return go_staged(k_das_staged<__nv_bfloat162, 4, 1, 8, 4, 8, kRing, 72, false>, 8, p, sm, s);
+    case V_ST64_C64_V4: return go_staged(k_das_staged<float2, 2, 2, 16, 4, 8, 8, 72, false>, 8, p, sm, s);
+    case V_ST64_H16_V4: return go_staged(k_das_staged<__half2, 4, 1, 16, 4, 8, 8, 72, false>, 8, p, sm, s);
+    case V_ST32_B16: return go_staged(k_das_staged<__nv_bfloat162, 4, 1, 8, 8, 8, kRing, 112, false>, 8, p, sm, s);
+    case V_ST64_B16_V4: return go_staged(k_das_staged<__nv_bfloat162, 4, 1, 16, 4, 8, 8, 72, false>, 8, p, sm, s);
     default: return cudaErrorInvalidValue;
   }
 }

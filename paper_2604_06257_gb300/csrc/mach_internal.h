@@ -100,6 +100,10 @@ struct DasParams {
   int* err;             // device error word (bit 0: a wait timed out)
   int debug_stall;      // test hook: the producer announces copies but never issues them
   int wb_x, wb_y, wb_z; // staged variants: voxel block of one warp inside the tile (0: row-major)
+  // staged variants with a plan-time term table only
+  const int64_t* tile_pairs;  // [tiles + 1] index of each tile's first pair (pairs in copy order)
+  const int4* pair_desc;      // [pairs] (transmit, element, first row, rows) of each copied window
+  const float4* term_rec;     // [pairs][voxel slots of a block] term records, in consumer order
 };
 
 // Tables built once per plan (kernel K1).
@@ -126,8 +130,16 @@ cudaError_t launch_das(const DasParams& p, Variant v, cudaStream_t s);
 // number of (tile, transmit, element) triples that need a copy.
 cudaError_t launch_tile_bounds(const DasParams& p, float4* tbox, float2* txr, int* d_rows_pairs,
                                cudaStream_t s);
-size_t staged_smem_bytes(Variant v, int rows_cap, int F, int T);
+size_t staged_smem_bytes(Variant v, int rows_cap, int F, int T, bool table);
 cudaError_t launch_das_staged(const DasParams& p, Variant v, cudaStream_t s);
+// Plan-time term table (k_das_table.cu): which staged variants have a table form, the
+// per-(tile, element) windows of every transmit (rows 0 = pair not used) and their
+// count, the pair list and records, and the table-mode launch.
+bool table_supported(Variant v);
+cudaError_t launch_pair_windows(const DasParams& p, int2* win, int* count, cudaStream_t s);
+cudaError_t launch_term_records(const DasParams& p, Variant v, const int2* win, const int64_t* first, int4* desc,
+                                float4* rec, cudaStream_t s);
+cudaError_t launch_das_table(const DasParams& p, Variant v, cudaStream_t s);
 cudaError_t launch_terms(const DasParams& p, const int64_t* vox_idx, int64_t n, int32_t* i0,
                          float* w, float* cw, cudaStream_t s);
 size_t das_smem_bytes(Variant v);

@@ -66,6 +66,7 @@ extern "C" mach_status mach_das_run_noalloc(const mach_das_desc* d, const void* 
                                             float* pd_dev_or_null, void* stream) {
   mach_status st = host_validate(d);
   if (st != MACH_OK) return st;
+  if (d->term_table) return MACH_ERR_UNSUPPORTED;   // a term table is plan state
   if (!iq_dev || (!y_dev_or_null && !pd_dev_or_null)) return MACH_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(iq_dev) & 15u) || (reinterpret_cast<uintptr_t>(y_dev_or_null) & 15u) ||
       (reinterpret_cast<uintptr_t>(pd_dev_or_null) & 3u))

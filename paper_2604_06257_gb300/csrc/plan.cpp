@@ -29,6 +29,11 @@ struct mach_plan_s {
   int rows_cap = 0;
   int64_t copy_pairs = 0;
   int64_t device_bytes = 0;
+  bool table = false;           // terms read from the plan-time term table
+  int64_t* d_tile_pairs = nullptr;
+  int4* d_pair_desc = nullptr;
+  float4* d_term_rec = nullptr;
+  int64_t table_bytes = 0;
 };
 
 namespace {
@@ -71,6 +76,7 @@ mach_status validate(const mach_das_desc* d) {
   if (!(d->f_number >= 0.0) || !std::isfinite(d->f_number)) return MACH_ERR_INVALID_ARG;
   if (d->apod < MACH_APOD_NONE || d->apod > MACH_APOD_GAUSS) return MACH_ERR_INVALID_ARG;
   if (d->iq_dtype < MACH_IQ_C64 || d->iq_dtype > MACH_IQ_C64_SPLIT) return MACH_ERR_INVALID_ARG;
+  if (d->term_table != 0 && d->term_table != 1) return MACH_ERR_INVALID_ARG;
   if (d->iq_dtype == MACH_IQ_C64_SPLIT && (d->n_frames % 4 != 0 || d->n_frames <= 4)) return MACH_ERR_UNSUPPORTED;
   if (d->n_samples < 2 || d->n_samples > (1 << 24)) return MACH_ERR_INVALID_ARG;
   if (d->n_frames < 1) return MACH_ERR_INVALID_ARG;
@@ -214,6 +220,9 @@ void release(mach_plan_s* p) {
   cudaFree(p->d_tbox);
   cudaFree(p->d_txr);
   cudaFree(p->d_err);
+  cudaFree(p->d_tile_pairs);
+  cudaFree(p->d_pair_desc);
+  cudaFree(p->d_term_rec);
   delete p;
 }
 
@@ -288,6 +297,70 @@ static mach_status configure_tiles(DasParams& b, Variant var, bool list, int64_t
   if (b.frame_tiles > 65535) return MACH_ERR_UNSUPPORTED;   // grid y limit
   if (static_cast<int64_t>(b.tiles_x) * b.tiles_y * b.tiles_z > INT32_MAX) return MACH_ERR_UNSUPPORTED;
   return MACH_OK;
+}
+
+// Plan-time term table (table mode): every usable (tile, element, transmit) pair's
+// window and the records of all voxel slots of the block, in the order a run consumes
+// them.  The windows come first; their counts, scanned on the host, give each pair its
+// index, and one block per (tile, element) then writes the records.
+static mach_status build_term_table(mach_plan_s* p, DasParams& b, cudaStream_t s) {
+  const int64_t tiles = static_cast<int64_t>(b.tiles_x) * b.tiles_y * b.tiles_z;
+  const int64_t n = tiles * b.C;
+  if (n > INT32_MAX) return MACH_ERR_UNSUPPORTED;   // one record block per (tile, element)
+  const VariantShape& sh = variant_shape(p->variant);
+  const int64_t nrec = static_cast<int64_t>(sh.warps) * sh.voxels_per_warp;
+  int2* d_win = nullptr;
+  int* d_count = nullptr;
+  int64_t* d_first = nullptr;
+  int64_t scratch = 0;
+  auto done = [&](mach_status e) {
+    cudaFree(d_win);
+    cudaFree(d_count);
+    cudaFree(d_first);
+    return e;
+  };
+  mach_status st;
+  if ((st = dev_alloc(reinterpret_cast<void**>(&d_win), sizeof(int2) * n * b.T, &scratch)) != MACH_OK) return done(st);
+  if ((st = dev_alloc(reinterpret_cast<void**>(&d_count), sizeof(int) * n, &scratch)) != MACH_OK) return done(st);
+  if (launch_pair_windows(b, d_win, d_count, s) != cudaSuccess) return done(MACH_ERR_CUDA);
+  std::vector<int> count(static_cast<size_t>(n));
+  if (cudaMemcpyAsync(count.data(), d_count, sizeof(int) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return done(MACH_ERR_CUDA);
+  std::vector<int64_t> first(static_cast<size_t>(n) + 1, 0);
+  for (int64_t i = 0; i < n; ++i) first[i + 1] = first[i] + count[i];
+  const int64_t pairs = first[n];
+  std::vector<int64_t> tile_first(static_cast<size_t>(tiles) + 1);
+  for (int64_t t = 0; t < tiles; ++t) tile_first[t] = first[t * b.C];
+  tile_first[tiles] = pairs;
+  const size_t bytes = sizeof(int64_t) * (tiles + 1) + sizeof(int4) * pairs + sizeof(float4) * pairs * nrec;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return done(MACH_ERR_CUDA);
+  }
+  if (bytes + sizeof(int64_t) * (n + 1) > free_b) return done(MACH_ERR_OOM);
+  if ((st = dev_alloc(reinterpret_cast<void**>(&p->d_tile_pairs), sizeof(int64_t) * (tiles + 1), &p->device_bytes)) != MACH_OK)
+    return done(st);
+  if ((st = dev_alloc(reinterpret_cast<void**>(&p->d_pair_desc), sizeof(int4) * pairs, &p->device_bytes)) != MACH_OK)
+    return done(st);
+  if ((st = dev_alloc(reinterpret_cast<void**>(&p->d_term_rec), sizeof(float4) * pairs * nrec, &p->device_bytes)) != MACH_OK)
+    return done(st);
+  if ((st = dev_alloc(reinterpret_cast<void**>(&d_first), sizeof(int64_t) * (n + 1), &scratch)) != MACH_OK)
+    return done(st);
+  if (cudaMemcpyAsync(d_first, first.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(p->d_tile_pairs, tile_first.data(), sizeof(int64_t) * (tiles + 1), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess)
+    return done(MACH_ERR_CUDA);
+  if (launch_term_records(b, p->variant, d_win, d_first, p->d_pair_desc, p->d_term_rec, s) != cudaSuccess)
+    return done(MACH_ERR_CUDA);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return done(MACH_ERR_CUDA);
+  b.tile_pairs = p->d_tile_pairs;
+  b.pair_desc = p->d_pair_desc;
+  b.term_rec = p->d_term_rec;
+  p->table_bytes = static_cast<int64_t>(bytes);
+  p->table = true;
+  return done(MACH_OK);
 }
 
 mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) {
@@ -454,9 +527,10 @@ mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) 
     b.tbox = p->d_tbox;
     b.txr = p->d_txr;
     b.rows_cap = p->rows_cap;
+    const bool tab = d->term_table != 0;
     const Variant smaller_ring = var == V_ST64_C64_V4 ? V_ST64_C64 : (var == V_ST64_H16_V4 ? V_ST64_H16 : var);
-    if (!forced && smaller_ring != var && staged_smem_bytes(var, p->rows_cap, F, T) > kStagedSmemCap &&
-        staged_smem_bytes(smaller_ring, p->rows_cap, F, T) <= kStagedSmemCap) {
+    if (!forced && smaller_ring != var && staged_smem_bytes(var, p->rows_cap, F, T, tab) > kStagedSmemCap &&
+        staged_smem_bytes(smaller_ring, p->rows_cap, F, T, tab) <= kStagedSmemCap) {
       // an 8-slot ring does not fit: the 2-pair variant needs only 4 slots (its tiles are
       // larger, so recompute them and their bounds)
       var = smaller_ring;
@@ -471,8 +545,8 @@ mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) 
       p->copy_pairs = stats[1];
       b.rows_cap = p->rows_cap;
     }
-    if (staged_smem_bytes(var, p->rows_cap, F, T) > kStagedSmemCap) {
-      if (forced) return fail(MACH_ERR_UNSUPPORTED);
+    if (staged_smem_bytes(var, p->rows_cap, F, T, tab) > kStagedSmemCap) {
+      if (forced || tab) return fail(MACH_ERR_UNSUPPORTED);
       // the tiles' windows are too long for the ring: use the L1-cached variant
       cudaFree(p->d_tbox);
       cudaFree(p->d_txr);
@@ -487,6 +561,11 @@ mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) 
       p->copy_pairs = 0;
       if ((st = configure_tiles(b, var, list, V, F)) != MACH_OK) return fail(st);
     }
+  }
+  if (d->term_table) {
+    // every term evaluated once here; runs read them instead of computing them
+    if (!variant_shape(var).staged || !table_supported(var)) return fail(MACH_ERR_UNSUPPORTED);
+    if ((st = build_term_table(p, b, s)) != MACH_OK) return fail(st);
   }
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(MACH_ERR_CUDA);
   cudaFree(d_raw);
@@ -516,7 +595,8 @@ static mach_status run(mach_plan p, const void* iq, float* pd, void* y, void* st
   q.iq = iq;
   q.y = static_cast<float2*>(y);
   q.pd = pd;
-  const cudaError_t e = launch_das(q, p->variant, static_cast<cudaStream_t>(stream));
+  const cudaError_t e = p->table ? launch_das_table(q, p->variant, static_cast<cudaStream_t>(stream))
+                                 : launch_das(q, p->variant, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? MACH_OK : MACH_ERR_CUDA;
 }
 
@@ -577,8 +657,9 @@ mach_status mach_plan_get_info(mach_plan p, mach_plan_info* info) {
   info->ring_rows = p->rows_cap;
   info->ring_slots = variant_shape(p->variant).ring_slots;
   info->copy_pairs = p->copy_pairs;
+  info->term_table_bytes = p->table_bytes;
   if (variant_shape(p->variant).staged) {
-    info->smem_bytes = static_cast<int64_t>(staged_smem_bytes(p->variant, p->rows_cap, p->base.F, p->base.T));
+    info->smem_bytes = static_cast<int64_t>(staged_smem_bytes(p->variant, p->rows_cap, p->base.F, p->base.T, p->table));
     info->threads_per_cta = (s.warps + 1) * 32;
   }
   return MACH_OK;

@@ -63,6 +63,7 @@ BAD = [
     dict(f_number=-0.5),
     dict(apod=7),
     dict(iq_dtype=5),
+    dict(term_table=2),
     dict(n_samples=1),
     dict(n_samples=(1 << 24) + 1),
     dict(n_frames=0),
@@ -161,3 +162,15 @@ def test_rf_to_iq_rejects_bad_arguments_before_cuda():
     bad = np.array([1.0, np.nan], dtype=np.float32)
     assert L.mach_rf_to_iq(fake, fake, 1, 1, 10, 1, 20e6, 5e6, 0.0, bad.ctypes.data, 2, 1, None) == \
         m.MACH_ERR_INVALID_ARG
+
+
+def test_term_table_is_plan_state_only():
+    """The allocation-free entry point and ragged batches have no term table: a
+    descriptor asking for one is refused before anything touches the device."""
+    d, keep = m.make_desc(**good_kwargs(term_table=True))
+    fake = C.c_void_p(256)
+    L = m.lib()
+    assert L.mach_das_run_noalloc(C.byref(d), fake, fake, None, None) == m.MACH_ERR_UNSUPPORTED
+    arr = (m.mach_das_desc * 1)(d)
+    h = C.c_void_p()
+    assert L.mach_batch_plan(arr, 1, None, None, C.byref(h)) == m.MACH_ERR_UNSUPPORTED
