@@ -260,17 +260,19 @@ __global__ void __launch_bounds__((NWC + 1) * 32) __maxnreg__(MAXR) k_das_staged
     }
     const SlotMeta mm = meta[my_slot];
     float4 rec = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
-    if (TABLE) {
+    if constexpr (TABLE) {
       if (mm.c >= 0) rec = slot_rec(my_slot)[warp * WV + rec_at];
-    } else if (mm.c >= 0) {
-      if (mm.c != cur_c) {
-        cur_c = mm.c;
-        geo.a = -1.f;
-        if (v_term >= 0) geo = term_geometry(vpos, mm.e, p);
-      }
-      if (geo.a >= 0.f) {
-        const float stx = tx_cached ? txc[mm.t * 32 + lane] : __ldg(&p.tx[static_cast<size_t>(mm.t) * p.V + v_term]);
-        rec = term_record(stx, geo, p);
+    } else {
+      if (mm.c >= 0) {
+        if (mm.c != cur_c) {
+          cur_c = mm.c;
+          geo.a = -1.f;
+          if (v_term >= 0) geo = term_geometry(vpos, mm.e, p);
+        }
+        if (geo.a >= 0.f) {
+          const float stx = tx_cached ? txc[mm.t * 32 + lane] : __ldg(&p.tx[static_cast<size_t>(mm.t) * p.V + v_term]);
+          rec = term_record(stx, geo, p);
+        }
       }
     }
     const int my_i0 = __float_as_int(rec.w);
