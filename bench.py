@@ -32,7 +32,8 @@ sys.path.insert(0, ROOT)
 METRIC = "DAS points/s (voxel x channel x transmit x frame, Eq. 1)"
 UNIT = "points/s"
 PAPER_POINTS_PER_S = 258_052_096 / 0.23e-3      # Sec. 4.2: 0.23 ms on an RTX 5090, 251^2 px
-KERNEL_SOURCES = ("k_das.cu", "k_das_staged.cu", "das_term.cuh", "tap_mac.cuh", "async_copy.cuh", "mach_internal.h")
+KERNEL_SOURCES = ("k_das.cu", "k_das_staged.cu", "das_staged.cuh", "k_das_table.cu", "das_term.cuh", "tap_mac.cuh",
+                  "async_copy.cuh", "mach_internal.h")
 FLUSH_BYTES = 256 << 20                           # > 129 MB L2
 
 
@@ -47,6 +48,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", default="", help="force a kernel variant (ablations)")
+    ap.add_argument("--term-table", action="store_true",
+                    help="time the plan that stores every term (mach_das_desc.term_table) instead of the "
+                         "on-the-fly delays")
     ap.add_argument("--ragged-n", type=int, default=64, help="instances of the ragged batch")
     ap.add_argument("--ragged-scale", type=float, default=1.0, help="grid scale of the ragged batch")
     ap.add_argument("--no-autotune", action="store_true")
@@ -243,7 +247,7 @@ def run_ours(args):
         iq = m.prepare_iq(iq_c64.permute(3, 0, 1, 2).contiguous(), "ftcs", args.iq_dtype)
     if args.variant:
         m.mach_debug_force_variant(args.variant)
-    plan = m.Plan(**m.plan_kwargs(acq))
+    plan = m.Plan(**m.plan_kwargs(acq), term_table=args.term_table)
     m.mach_debug_force_variant(None)
     info = plan.info()
     V, F = acq.n_vox, acq.n_frames
@@ -298,7 +302,7 @@ def run_ours(args):
     achieved = flops / t_launch / 1e12
     comp = counts.compulsory_bytes(V, acq.n_elem, acq.n_tx, acq.n_samples, F, write_y=True, write_pd=True,
                                    iq_bytes=8 if args.iq_dtype in ("c64", "c64split") else 4)
-    traffic = profiled_traffic(info["variant"], acq.name)
+    traffic = profiled_traffic(info["variant"] + ("+table" if args.term_table else ""), acq.name)
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": traffic,
             "kernel": info["variant"],
@@ -359,9 +363,10 @@ def run_ours(args):
             alt["c64_interleaved"] = {"value": acq.points / tt, "ms_per_step": tt * 1e3,
                                       "variant": pi.info()["variant"]}
         # the same step reading every term from a plan-time table (mach_das_desc.term_table)
-        # instead of evaluating it, and its check against the on-the-fly result
+        # instead of evaluating it (or, when that is the timed plan, the on-the-fly one), and
+        # the check that both give the same bits
         try:
-            pt = m.Plan(**m.plan_kwargs(acq), term_table=True)
+            pt = m.Plan(**m.plan_kwargs(acq), term_table=not args.term_table)
         except m.MachError as e:
             alt["term_table"] = {"unavailable": str(e)}
         else:
@@ -384,9 +389,10 @@ def run_ours(args):
                 m.mach_power_doppler(plan.handle, iq, pd, y)
                 torch.cuda.synchronize()
                 ti = pt.info()
-                alt["term_table"] = {"value": acq.points / tt, "ms_per_step": tt * 1e3, "variant": ti["variant"],
+                alt["on_the_fly_delays" if args.term_table else "term_table"] = {
+                                     "value": acq.points / tt, "ms_per_step": tt * 1e3, "variant": ti["variant"],
                                      "table_bytes": ti["term_table_bytes"],
-                                     "bitwise_equal_to_on_the_fly": bool(torch.equal(y_t, y) and torch.equal(pd_t, pd))}
+                                     "bitwise_equal": bool(torch.equal(y_t, y) and torch.equal(pd_t, pd))}
 
     # end to end through the public API with host buffers (pinned), copies timed: the host
     # holds complex64 IQ in acquisition order; each step copies one acquisition in,
@@ -440,6 +446,9 @@ def run_ours(args):
                                                               "c64": "interleaved complex64"}.get(args.iq_dtype,
                                                                                                   args.iq_dtype),
                                                 "kernel_variant": info["variant"],
+                                                "delays": ("term table (every term evaluated at plan time)"
+                                                           if args.term_table else
+                                                           "hybrid: transmit table + receive delays on the fly"),
                                                 "active_fraction": active_terms / (V * acq.n_elem * acq.n_tx)}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "plan": info, "k0_iq_convert": k0,
                 "other_layouts": alt,
