@@ -226,7 +226,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--bank", type=int, default=1024)
     ap.add_argument("--samples", type=int, default=4000)
-    ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--epochs", type=int, default=12)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
