@@ -314,7 +314,11 @@ def run_ours(args):
                     "peak_gbs": hbm_peak, "frac": comp / t_launch / 1e9 / hbm_peak},
             "sm_load_path": {"bytes_per_term_frame": 16 if args.iq_dtype in ("c64", "c64split") else 8,
                              "achieved_gbs": active_points * (16 if args.iq_dtype in ("c64", "c64split") else 8)
-                             / t_launch / 1e9}}
+                             / t_launch / 1e9,
+                             "peak_gbs": n_sm * 128 * sm_max * 1e6 / 1e9,
+                             "peak_source": f"shared-memory load path: {n_sm} SMs x 128 B/clk x {sm_max:.0f} MHz",
+                             "frac": active_points * (16 if args.iq_dtype in ("c64", "c64split") else 8)
+                             / t_launch / (n_sm * 128 * sm_max * 1e6)}}
 
     # K0 (channel-data preparation): acquisition order -> frame-contiguous layout, per
     # storage type; HBM-bound, so it is reported against the measured copy bandwidth
