@@ -94,9 +94,20 @@ mach_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? MACH_OK : MACH_ER
     if (st_ != MACH_OK) return st_;          \
   } while (0)
 
+// The tensor-core kernel takes at most 256 output channels.  A convolution's data gradient
+// is a convolution from co to ci channels, so the one of a decoder convolution fed by
+// 256 + 128 channels (five levels) runs on the warp-MMA kernel, whose bfloat16 weight
+// copies are then kept current too.
+bool fwd_on_tc(const mach_unet_s* u, const Conv& c) {
+  return u->backend == MACH_UNET_TCGEN05 && conv_tc_supported(c.ci, c.co);
+}
+bool dgrad_on_tc(const mach_unet_s* u, const Conv& c) {
+  return u->backend == MACH_UNET_TCGEN05 && conv_tc_supported(c.co, c.ci);
+}
+
 mach_status conv_fwd(mach_unet_s* u, const Conv& c, cudaStream_t s) {
   const int l = c.level;
-  if (u->backend == MACH_UNET_TCGEN05)
+  if (fwd_on_tc(u, c))
     return cuda_ok(launch_conv_tc(c.in->p, c.wpk, u->params + c.b_off, c.out ? c.out->p : nullptr,
                                   c.out ? nullptr : u->o, u->N, u->nz[l], u->ny[l], u->nx[l], c.ci, c.co, 0,
                                   c.act ? 1 : 0, s));
@@ -109,7 +120,7 @@ mach_status conv_bwd(mach_unet_s* u, const Conv& c, void* gout, void* gin, cudaS
   const int l = c.level;
   TRY(mach_nn_conv3d_wgrad(c.in->p, gout, u->grads + c.w_off, u->N, u->nz[l], u->ny[l], u->nx[l], c.ci, c.co, s));
   TRY(mach_nn_bias_grad(gout, u->grads + c.b_off, u->vox(l), c.co, s));
-  if (gin && u->backend == MACH_UNET_TCGEN05)
+  if (gin && dgrad_on_tc(u, c))
     TRY(cuda_ok(launch_conv_tc(gout, c.wpkt, nullptr, gin, nullptr, u->N, u->nz[l], u->ny[l], u->nx[l], c.co, c.ci,
                                1, 0, s)));
   else if (gin)
@@ -432,8 +443,10 @@ mach_status mach_unet_train_step(mach_unet net, const void* x, const void* targe
   const bool tc = net->backend == MACH_UNET_TCGEN05;
   for (const Conv& c : net->convs) {
     const int64_t nw = 27LL * c.ci * c.co;
+    const bool copies = !fwd_on_tc(net, c) || !dgrad_on_tc(net, c);   // warp-MMA kernels read them
     TRY(mach_nn_adam(net->params + c.w_off, net->adam_m + c.w_off, net->adam_v + c.w_off, net->grads + c.w_off, nw,
-                     lr, 0.9f, 0.999f, 1e-8f, net->step, tc ? nullptr : c.wb, tc ? nullptr : c.wbt, c.ci, c.co, s));
+                     lr, 0.9f, 0.999f, 1e-8f, net->step, copies ? c.wb : nullptr, copies ? c.wbt : nullptr, c.ci,
+                     c.co, s));
     if (tc) TRY(cuda_ok(launch_pack_weights(net->params + c.w_off, c.wpk, c.wpkt, c.ci, c.co, s)));
     TRY(mach_nn_adam(net->params + c.b_off, net->adam_m + c.b_off, net->adam_v + c.b_off, net->grads + c.b_off, c.co,
                      lr, 0.9f, 0.999f, 1e-8f, net->step, nullptr, nullptr, 0, 0, s));

@@ -160,7 +160,8 @@ def evaluate(net, bank: Bank, W: np.ndarray, gain: float) -> Dict[str, float]:
 
 
 def train(n: int = 128, bank_size: int = 512, samples: int = 2000, epochs: int = 4, batch: int = 8,
-          lr: float = 5e-4, seed: int = 0, test_blocks: int = 128, test_scenes: int = 64, log=print):
+          lr: float = 5e-4, seed: int = 0, test_blocks: int = 128, test_scenes: int = 64, levels: int = 4,
+          base_ch: int = 16, log=print):
     """Train a network from scratch; returns (net, report)."""
     import torch
 
@@ -172,7 +173,7 @@ def train(n: int = 128, bank_size: int = 512, samples: int = 2000, epochs: int =
     torch.cuda.synchronize()
     t_data = time.time() - t0
     gain = ls_gain(bank)
-    net = UNet(n, n, n, batch, levels=4, base_ch=16, seed=seed)
+    net = UNet(n, n, n, batch, levels=levels, base_ch=base_ch, seed=seed)
     net.set_gain(gain)
     Wtr = scene_weights(rng, bank_size, samples)
     Wte = scene_weights(np.random.default_rng(seed + 7), test_blocks, test_scenes)
@@ -198,7 +199,7 @@ def train(n: int = 128, bank_size: int = 512, samples: int = 2000, epochs: int =
     torch.cuda.synchronize()
     t_train = time.time() - t1
     after = evaluate(net, test, Wte, gain)
-    report = {"n": n, "bank_blocks": bank_size, "train_scenes": samples, "epochs": epochs, "batch": batch,
+    report = {"n": n, "levels": levels, "base_ch": base_ch, "bank_blocks": bank_size, "train_scenes": samples, "epochs": epochs, "batch": batch,
               "lr": lr, "steps": steps, "gain": gain, "data_s": t_data, "train_s": t_train,
               "ms_per_step": 1e3 * t_train / steps, "test_blocks": test_blocks, "test_scenes": test_scenes,
               "untrained": before, "trained": after, "loss_history": hist}
@@ -230,10 +231,12 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--levels", type=int, default=4)
+    ap.add_argument("--base-ch", type=int, default=16)
     ap.add_argument("--out", default=os.path.join(WEIGHTS_DIR, "unet_few3_many21_128.npz"))
     ap.add_argument("--report", default=None)
     a = ap.parse_args(argv)
-    net, rep = train(a.n, a.bank, a.samples, a.epochs, a.batch, a.lr, a.seed)
+    net, rep = train(a.n, a.bank, a.samples, a.epochs, a.batch, a.lr, a.seed, levels=a.levels, base_ch=a.base_ch)
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
     save(net, rep["gain"], a.out)
     rep["weights"] = os.path.basename(a.out)

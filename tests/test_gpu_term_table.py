@@ -54,6 +54,17 @@ def test_table_bitwise_equals_on_the_fly_2d(F, dt):
     assert info["variant"].startswith("staged")
 
 
+def test_table_many_transmits():
+    """More transmits than the on-the-fly kernel caches per warp (16): it then reads the
+    transmit delays from global memory; the table must still give the same bits."""
+    acq = small_random(32, C=9, T=21, S=400, iq_dtype="c64split", grid=(21, 1, 17))
+    iq = synth.random_iq(acq, 21, device="cuda")
+    diq = dev_iq(acq, iq)
+    info, y, pd = both_modes(acq, diq)
+    assert info["variant"].startswith("staged")
+    compare(acq, synth.iqmod.from_storage(diq).cpu(), y, pd)
+
+
 def test_table_unsupported_when_windows_exceed_the_ring():
     """Where the on-the-fly plan falls back to an L1-path kernel because the sample
     windows do not fit the ring, a table plan is refused (no table form)."""
