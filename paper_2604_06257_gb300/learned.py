@@ -161,7 +161,7 @@ def evaluate(net, bank: Bank, W: np.ndarray, gain: float) -> Dict[str, float]:
 
 def train(n: int = 128, bank_size: int = 512, samples: int = 2000, epochs: int = 4, batch: int = 8,
           lr: float = 5e-4, seed: int = 0, test_blocks: int = 128, test_scenes: int = 64, levels: int = 4,
-          base_ch: int = 16, log=print):
+          base_ch: int = 16, warmup: int = 0, log=print):
     """Train a network from scratch; returns (net, report)."""
     import torch
 
@@ -191,6 +191,8 @@ def train(n: int = 128, bank_size: int = 512, samples: int = 2000, epochs: int =
             fx, fy = bool(rng.integers(2)), bool(rng.integers(2))
             x, t = flip(x, n, fx, fy), flip(t, n, fx, fy)
             lr_t = lr * (0.05 + 0.95 * 0.5 * (1 + math.cos(math.pi * step / steps)))
+            if step < warmup:                                   # linear warm-up
+                lr_t *= (step + 1) / warmup
             net.train_step(x.contiguous(), t.contiguous(), lr_t, loss)
             step += 1
             if step % 25 == 0 or step == steps:
@@ -199,7 +201,7 @@ def train(n: int = 128, bank_size: int = 512, samples: int = 2000, epochs: int =
     torch.cuda.synchronize()
     t_train = time.time() - t1
     after = evaluate(net, test, Wte, gain)
-    report = {"n": n, "levels": levels, "base_ch": base_ch, "bank_blocks": bank_size, "train_scenes": samples, "epochs": epochs, "batch": batch,
+    report = {"n": n, "levels": levels, "base_ch": base_ch, "warmup": warmup, "bank_blocks": bank_size, "train_scenes": samples, "epochs": epochs, "batch": batch,
               "lr": lr, "steps": steps, "gain": gain, "data_s": t_data, "train_s": t_train,
               "ms_per_step": 1e3 * t_train / steps, "test_blocks": test_blocks, "test_scenes": test_scenes,
               "untrained": before, "trained": after, "loss_history": hist}
@@ -233,10 +235,12 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--levels", type=int, default=4)
     ap.add_argument("--base-ch", type=int, default=16)
+    ap.add_argument("--warmup", type=int, default=0, help="steps of linear learning-rate warm-up")
     ap.add_argument("--out", default=os.path.join(WEIGHTS_DIR, "unet_few3_many21_128.npz"))
     ap.add_argument("--report", default=None)
     a = ap.parse_args(argv)
-    net, rep = train(a.n, a.bank, a.samples, a.epochs, a.batch, a.lr, a.seed, levels=a.levels, base_ch=a.base_ch)
+    net, rep = train(a.n, a.bank, a.samples, a.epochs, a.batch, a.lr, a.seed, levels=a.levels, base_ch=a.base_ch,
+                     warmup=a.warmup)
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
     save(net, rep["gain"], a.out)
     rep["weights"] = os.path.basename(a.out)
