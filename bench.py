@@ -643,18 +643,36 @@ def run_learned(args):
 
     # end to end through the public API: the 3-angle IQ in the scanner's order from pinned
     # host memory, K0 to split rows, DAS, U-Net, the prediction back to pinned host
-    # memory; copies inside the timed region
+    # memory; copies inside the timed region.  Two staging sets and separate upload /
+    # download streams let step k+1's upload and step k-1's download overlap step k's
+    # beamforming and network (events order the reuse of each set)
     iq_pin = few_scanner.cpu().pin_memory()
     out_pin = torch.empty((V, B), dtype=torch.complex64).pin_memory()
-    scan_dev = torch.empty_like(few_scanner)
+    scan_dev = [torch.empty_like(few_scanner) for _ in range(2)]
+    pred2 = [pred, torch.empty_like(pred)]
     Tf = len(Lc.FEW_IN_MANY)
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+    ev = {k: [torch.cuda.Event(), torch.cuda.Event()] for k in ("up", "read", "done", "down")}
+    state = {"k": 0}
 
     def e2e_step():
-        scan_dev.copy_(iq_pin, non_blocking=True)
-        m.mach_iq_convert(scan_dev, "ftcs", iq_few, "c64split", Tf, C, S, B)
-        pf.run(iq_few, y_few)
-        net.forward(y_few, pred)
-        out_pin.copy_(pred, non_blocking=True)
+        b = state["k"] % 2
+        state["k"] += 1
+        with torch.cuda.stream(up):
+            up.wait_event(ev["read"][b])            # K0 of step k-2 has read this set
+            scan_dev[b].copy_(iq_pin, non_blocking=True)
+            ev["up"][b].record(up)
+        stream.wait_event(ev["up"][b])
+        m.mach_iq_convert(scan_dev[b], "ftcs", iq_few, "c64split", Tf, C, S, B, stream)
+        ev["read"][b].record(stream)
+        pf.run(iq_few, y_few, stream)
+        stream.wait_event(ev["down"][b])            # step k-2's prediction has been read back
+        net.forward(y_few, pred2[b], stream)
+        ev["done"][b].record(stream)
+        with torch.cuda.stream(down):
+            down.wait_event(ev["done"][b])
+            out_pin.copy_(pred2[b], non_blocking=True)
+            ev["down"][b].record(down)
 
     for _ in range(3):
         e2e_step()
