@@ -786,6 +786,82 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_rf(args):
+    """RF input on the 2D Power Doppler geometry: real RF at 4x the IQ rate (83.2 MHz, 8189
+    samples per channel and frame) demodulated, low-passed (32 taps) and decimated into the
+    complex64 IQ the beamformer reads (mach_rf_to_iq), then beamformed with Power Doppler.
+    Timed: the demodulation alone, and demodulation + beamforming per acquisition."""
+    import torch
+    import synth
+    import paper_2604_06257_gb300 as m
+    from paper_2604_06257_gb300 import build as pkg_build
+    from synth.iq import lowpass_taps
+
+    pkg_build.build()
+    m.lib()
+    acq = synth.make_acquisition("doppler2d", "full", "c64")
+    decim, L = 4, 32
+    T, C, S, F = acq.iq_shape
+    S_rf = decim * (S - 1) + 1
+    fs_rf = acq.fs * decim
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    rf = torch.randn((T, C, S_rf, F), generator=g, device="cuda")   # values do not change the timing
+    taps = lowpass_taps(L, acq.fc, fs_rf)
+    iq = torch.empty((T, C, S, F), dtype=torch.complex64, device="cuda")
+    plan = m.Plan(**m.plan_kwargs(acq))
+    pd = torch.empty(acq.n_vox, dtype=torch.float32, device="cuda")
+    y = torch.empty((acq.n_vox, F), dtype=torch.complex64, device="cuda")
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def demod():
+        m.mach_rf_to_iq(rf, taps, fs_rf, acq.fc, acq.t0, decim, iq)
+
+    def both():
+        demod()
+        m.mach_power_doppler(plan.handle, iq, pd, y)
+
+    def timed(fn, steps):
+        for _ in range(max(3, args.warmup)):
+            flush.zero_()
+            fn()
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(b) for a, b in evs) / 1e3
+
+    steps = max(1, min(args.steps, 500))
+    t_demod = timed(demod, steps)
+    t_both = timed(both, steps)
+    n_iq = T * C * S * F
+    byts = 4 * T * C * S_rf * F + 8 * n_iq                 # RF read once, IQ written once
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    line = {"metric": "DAS points/s from RF input (demodulation + beamforming + Power Doppler)",
+            "value": acq.points / t_both, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": t_both * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{acq.name} from RF: {S_rf} RF samples per channel and frame at "
+                                   f"{fs_rf / 1e6:.1f} MHz, {L}-tap low-pass, decimation {decim}",
+                       "l2": "flushed between steps (256 MB write)"},
+            "demodulation": {"ms": t_demod * 1e3, "iq_samples_per_s": n_iq / t_demod,
+                             "bytes": byts, "achieved_gbs": byts / t_demod / 1e9, "peak_gbs": hbm,
+                             "frac": byts / t_demod / 1e9 / hbm},
+            "gpu_launches": 2 * steps}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -794,6 +870,8 @@ def main():
         run_ragged(args)
     elif args.workload == "learned3d":
         run_learned(args)
+    elif args.workload == "rf2d":
+        run_rf(args)
     else:
         run_ours(args)
     try:

@@ -8,8 +8,11 @@
 // point, Phi + m R (mod 2^32) with Phi = round(2^32 frac(fc t0)) and R = round(2^32 frac(fc
 // / fs)), the same construction the DAS kernels use for the inverse rotation.
 //
-// One thread per output sample; consecutive threads take consecutive frames, so every RF
-// tap read is coalesced over the frame axis.
+// One block per (transmit, element) row and run of kRfNB output samples.  The mixing
+// phasor depends only on the RF sample index, so the block evaluates it once per RF sample
+// of its window into shared memory (instead of once per tap of every output); threads then
+// take (output sample, frame) pairs, consecutive threads consecutive frames, so every RF tap
+// read is coalesced over the frame axis.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -30,29 +33,47 @@ struct RfParams {
   float h[kMaxTaps];
 };
 
+constexpr int kRfNB = 64;   // output samples per block
+
+// grid: (rows, runs of kRfNB output samples); dynamic shared memory: the block's phasors
 __global__ void __launch_bounds__(256) k_rf_to_iq(const RfParams p) {
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t total = p.rows * p.s_iq * p.F;
-  if (i >= total) return;
-  const int f = static_cast<int>(i % p.F);
-  const int64_t q = i / p.F;
-  const int n = static_cast<int>(q % p.s_iq);
-  const int64_t row = q / p.s_iq;
-  const float* src = p.rf + row * static_cast<int64_t>(p.s_rf) * p.F + f;
-  const int m0 = n * p.decim - (p.L - 1) / 2;
-  float re = 0.f, im = 0.f;
-  for (int k = 0; k < p.L; ++k) {
-    const int m = m0 + k;
-    if (m < 0 || m >= p.s_rf) continue;
-    const float x = p.h[k] * __ldg(src + static_cast<int64_t>(m) * p.F);
-    // exp(-j 2 pi phase): phase in cycles as a signed 32-bit fraction of a turn
-    const uint32_t ph = p.phi + static_cast<uint32_t>(m) * p.r;
-    float s, c;
-    sincospif(static_cast<float>(static_cast<int32_t>(ph)) * 0x1.0p-31f, &s, &c);
-    re = fmaf(x, c, re);
-    im = fmaf(-x, s, im);
+  extern __shared__ float2 rot[];   // (cos, sin) of the carrier phase of RF samples m_lo ...
+  const int64_t row = blockIdx.x;
+  const int n0 = blockIdx.y * kRfNB;
+  const int nb = min(kRfNB, p.s_iq - n0);
+  const int m_lo = n0 * p.decim - (p.L - 1) / 2;
+  const int span = (nb - 1) * p.decim + p.L;   // RF samples the block's outputs reach
+  for (int j = threadIdx.x; j < span; j += blockDim.x) {
+    const int m = m_lo + j;
+    float s = 0.f, c = 0.f;
+    if (m >= 0 && m < p.s_rf) {
+      // exp(-j 2 pi phase): phase in cycles as a signed 32-bit fraction of a turn
+      const uint32_t ph = p.phi + static_cast<uint32_t>(m) * p.r;
+      sincospif(static_cast<float>(static_cast<int32_t>(ph)) * 0x1.0p-31f, &s, &c);
+    }
+    rot[j] = make_float2(c, s);
   }
-  p.iq[i] = make_float2(re, im);
+  __syncthreads();
+  const float* base = p.rf + row * static_cast<int64_t>(p.s_rf) * p.F;
+  float2* out = p.iq + (row * p.s_iq + n0) * static_cast<int64_t>(p.F);
+  const int outputs = nb * p.F;
+  for (int o = threadIdx.x; o < outputs; o += blockDim.x) {
+    const int nl = o / p.F, f = o - nl * p.F;
+    const int j0 = nl * p.decim;                 // rot index of tap 0
+    const int m0 = m_lo + j0;                    // RF sample of tap 0
+    // taps whose RF sample exists, so that the loop runs without a branch
+    const int k_lo = max(0, -m0), k_hi = min(p.L, p.s_rf - m0);
+    const float* src = base + f;
+    float re = 0.f, im = 0.f;
+#pragma unroll 8
+    for (int k = k_lo; k < k_hi; ++k) {
+      const float x = p.h[k] * __ldg(src + static_cast<int64_t>(m0 + k) * p.F);
+      const float2 cs = rot[j0 + k];
+      re = fmaf(x, cs.x, re);
+      im = fmaf(-x, cs.y, im);
+    }
+    out[o] = make_float2(re, im);
+  }
 }
 
 namespace {
@@ -91,8 +112,11 @@ extern "C" mach_status mach_rf_to_iq(const float* rf, void* iq, int32_t n_tx, in
     if (!std::isfinite(taps[k])) return MACH_ERR_INVALID_ARG;
     p.h[k] = taps[k];
   }
-  const int64_t total = p.rows * p.s_iq * p.F;
-  if ((total + 255) / 256 > 0x7fffffffLL) return MACH_ERR_UNSUPPORTED;
-  k_rf_to_iq<<<static_cast<unsigned>((total + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(p);
+  const int64_t runs = (p.s_iq + kRfNB - 1) / kRfNB;
+  if (runs > 65535 || p.rows > 0x7fffffffLL) return MACH_ERR_UNSUPPORTED;   // grid limits
+  const size_t smem = sizeof(float2) * static_cast<size_t>((kRfNB - 1) * decim + n_taps);
+  if (smem > 48 * 1024) return MACH_ERR_UNSUPPORTED;   // (decimation above ~95)
+  k_rf_to_iq<<<dim3(static_cast<unsigned>(p.rows), static_cast<unsigned>(runs)), 256, smem,
+               static_cast<cudaStream_t>(stream)>>>(p);
   return cudaGetLastError() == cudaSuccess ? MACH_OK : MACH_ERR_CUDA;
 }
