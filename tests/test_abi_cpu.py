@@ -174,3 +174,17 @@ def test_term_table_is_plan_state_only():
     arr = (m.mach_das_desc * 1)(d)
     h = C.c_void_p()
     assert L.mach_batch_plan(arr, 1, None, None, C.byref(h)) == m.MACH_ERR_UNSUPPORTED
+
+
+def test_rf_to_iq_size_limits_refused_before_launch():
+    """More than 65535 runs of 64 output samples (the grid's second axis), or a decimation
+    whose phasor window exceeds 48 KB of shared memory, are refused before any launch."""
+    L = m.lib()
+    fake = C.c_void_p(256)
+    h = np.ones(8, dtype=np.float32)
+    # 65536 * 64 + 1 IQ samples per channel at decimation 1
+    assert L.mach_rf_to_iq(fake, fake, 1, 1, 65536 * 64 + 1, 1, 20e6, 5e6, 0.0, h.ctypes.data, 8, 1,
+                           None) == m.MACH_ERR_UNSUPPORTED
+    # (63 * decim + taps) complex phasors over 48 KB
+    assert L.mach_rf_to_iq(fake, fake, 1, 1, 100000, 1, 20e6, 5e6, 0.0, h.ctypes.data, 8, 100,
+                           None) == m.MACH_ERR_UNSUPPORTED
