@@ -184,7 +184,8 @@ mach_status mach_iq_convert(const void *src_dev, int32_t src_order, void *dst_de
  * stops 2 fc, iq approximates (A / 2) g(t - tau) exp(-j 2 pi fc tau), the IQ model of the
  * plan.  Arguments are checked before the launch; MACH_ERR_INVALID_ARG for bad sizes,
  * rates, taps or alignment; MACH_ERR_UNSUPPORTED above 4,194,240 IQ samples per channel
- * and frame, or when 63 decim + n_taps exceeds 6144 (decimation above about 95); CUDA.
+ * and frame, above 2^24 frames, or when 63 decim + n_taps exceeds 6144 (decimation above
+ * about 95); CUDA.
  * Stream-ordered, asynchronous. */
 mach_status mach_rf_to_iq(const float *rf_dev, void *iq_dev, int32_t n_tx, int32_t n_elem, int32_t n_rf,
                           int32_t n_frames, double fs_rf, double fc, double t0, const float *taps,

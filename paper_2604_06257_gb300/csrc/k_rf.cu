@@ -114,6 +114,7 @@ extern "C" mach_status mach_rf_to_iq(const float* rf, void* iq, int32_t n_tx, in
   }
   const int64_t runs = (p.s_iq + kRfNB - 1) / kRfNB;
   if (runs > 65535 || p.rows > 0x7fffffffLL) return MACH_ERR_UNSUPPORTED;   // grid limits
+  if (n_frames > (1 << 24)) return MACH_ERR_UNSUPPORTED;                      // kRfNB * F in 32 bits
   const size_t smem = sizeof(float2) * static_cast<size_t>((kRfNB - 1) * decim + n_taps);
   if (smem > 48 * 1024) return MACH_ERR_UNSUPPORTED;   // (decimation above ~95)
   k_rf_to_iq<<<dim3(static_cast<unsigned>(p.rows), static_cast<unsigned>(runs)), 256, smem,

@@ -188,3 +188,6 @@ def test_rf_to_iq_size_limits_refused_before_launch():
     # (63 * decim + taps) complex phasors over 48 KB
     assert L.mach_rf_to_iq(fake, fake, 1, 1, 100000, 1, 20e6, 5e6, 0.0, h.ctypes.data, 8, 100,
                            None) == m.MACH_ERR_UNSUPPORTED
+    # more than 2^24 frames (a block's outputs are counted in 32 bits)
+    assert L.mach_rf_to_iq(fake, fake, 1, 1, 100, (1 << 24) + 1, 20e6, 5e6, 0.0, h.ctypes.data, 8, 1,
+                           None) == m.MACH_ERR_UNSUPPORTED
