@@ -191,7 +191,6 @@ mach_status mach_rf_to_iq(const float *rf_dev, void *iq_dev, int32_t n_tx, int32
                           int32_t n_frames, double fs_rf, double fc, double t0, const float *taps,
                           int32_t n_taps, int32_t decim, void *stream);
 
-/* Release a plan and its device tables (synchronises the device).  NULL is a no-op. */
 /* Uncompounded output (the output shape of the paper's memory table, Table 3: voxels x
  * compounded planes x frames): y_dev complex64 [n_vox][n_tx][n_frames], element
  * (v, t, f) = the delay-and-sum of transmit t alone, i.e. the terms of transmit t of
@@ -201,6 +200,7 @@ mach_status mach_rf_to_iq(const float *rf_dev, void *iq_dev, int32_t n_tx, int32
  * alignment the plan's kernel uses). */
 mach_status mach_das_run_per_tx(mach_plan p, const void *iq_dev, void *y_dev, void *stream);
 
+/* Release a plan and its device tables (synchronises the device).  NULL is a no-op. */
 mach_status mach_plan_destroy(mach_plan p);
 
 /* Static, NUL-terminated description of a status code. */
@@ -303,9 +303,12 @@ mach_status mach_plan_device_status(mach_plan p, void *stream);
  * call), iq_dev as for mach_das_run, outputs y_dev_or_null (complex64 [n_vox][n_frames])
  * and/or pd_dev_or_null (float32 [n_vox]), at least one of them.
  * Errors: INVALID_ARG as for a plan or a NULL/misaligned buffer; UNSUPPORTED when the
- * tables (16 B per voxel + 4 B per voxel and transmit + 16 B per element, plus 12 B per
- * voxel for a voxel list and 4 B per voxel and frame tile for Power Doppler over more
- * than one frame tile) exceed the 8 MiB array; CUDA.  Nothing is launched on error.
+ * tables exceed the 8 MiB array.  The tables are, each rounded up to a multiple of 256 B:
+ * 16 B per voxel; 16 B per element; 4 B per voxel and transmit; 24 B per transmit for
+ * plane waves (none with tx_table_dev); 12 B per voxel for a voxel list; 4 B per voxel
+ * and frame tile for Power Doppler over more than one frame tile.  CUDA on a failed
+ * copy or launch (the runtime's last error is cleared).  Nothing is enqueued on argument
+ * errors or when the tables do not fit.
  * The first call on a device looks up the array's device address (do it before any
  * stream capture).  Calls share the array, so calls that overlap on the GPU race;
  * order them on one stream.  Returns after the host arrays are copied; the

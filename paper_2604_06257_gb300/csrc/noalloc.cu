@@ -30,6 +30,13 @@ namespace {
 constexpr size_t kScratchBytes = size_t{8} << 20;   // 8 MiB
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
+// A failed CUDA call leaves its error as the runtime's last error; clear it so that the
+// caller's next launch check does not report this call's failure again.
+mach_status cuda_fail() {
+  cudaGetLastError();
+  return MACH_ERR_CUDA;
+}
+
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char* g_scratch_dev[kMaxDevices] = {};
@@ -37,18 +44,12 @@ unsigned char* g_scratch_dev[kMaxDevices] = {};
 // Device address of g_scratch on the current device (set up on first use).
 mach_status scratch_address(unsigned char** out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
-    cudaGetLastError();
-    return MACH_ERR_CUDA;
-  }
+  if (cudaGetDevice(&dev) != cudaSuccess) return cuda_fail();
   if (dev < 0 || dev >= kMaxDevices) return MACH_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_scratch_dev[dev]) {
     void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) {
-      cudaGetLastError();
-      return MACH_ERR_CUDA;
-    }
+    if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) return cuda_fail();
     g_scratch_dev[dev] = static_cast<unsigned char*>(ptr);
   }
   *out = g_scratch_dev[dev];
@@ -130,11 +131,11 @@ extern "C" mach_status mach_das_run_noalloc(const mach_das_desc* d, const void* 
 
   // host arrays -> scratch (pageable copies return once the host data has been taken)
   if (cudaMemcpyAsync(d_elem, elem.data(), sizeof(float4) * C, cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return MACH_ERR_CUDA;
+    return cuda_fail();
   if (d_u && cudaMemcpyAsync(d_u, u.data(), sizeof(double) * u.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return MACH_ERR_CUDA;
+    return cuda_fail();
   if (d_raw && cudaMemcpyAsync(d_raw, d->vox_pos, sizeof(float) * 3 * V, cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return MACH_ERR_CUDA;
+    return cuda_fail();
 
   TableParams tp{};
   tp.raw_vox = d_raw;
@@ -154,7 +155,7 @@ extern "C" mach_status mach_das_run_noalloc(const mach_das_desc* d, const void* 
   tp.T = T;
   tp.vox_out = d_vox;
   tp.tx_out = d_tx;
-  if (launch_tables(tp, s) != cudaSuccess) return MACH_ERR_CUDA;
+  if (launch_tables(tp, s) != cudaSuccess) return cuda_fail();
 
   b.vox = d_vox;
   b.elem = d_elem;
@@ -179,5 +180,5 @@ extern "C" mach_status mach_das_run_noalloc(const mach_das_desc* d, const void* 
   b.r_f = static_cast<float>(d->fc / d->fs);
   b.phase_R = host_fixed_cycles(d->fc / d->fs);
   b.phase_Phi = host_fixed_cycles(d->fc * d->t0);
-  return launch_das(b, var, s) == cudaSuccess ? MACH_OK : MACH_ERR_CUDA;
+  return launch_das(b, var, s) == cudaSuccess ? MACH_OK : cuda_fail();
 }
