@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "DAS points/s (voxel x channel x transmit x frame, Eq. 1)"
 UNIT = "points/s"
 PAPER_POINTS_PER_S = 258_052_096 / 0.23e-3      # Sec. 4.2: 0.23 ms on an RTX 5090, 251^2 px
-KERNEL_SOURCES = ("k_das.cu", "k_das_staged.cu", "das_staged.cuh", "k_das_table.cu", "das_term.cuh", "tap_mac.cuh",
+KERNEL_SOURCES = ("k_das.cu", "k_das_staged.cu", "k_das_exact.cu", "das_staged.cuh", "k_das_table.cu", "das_term.cuh", "tap_mac.cuh",
                   "async_copy.cuh", "mach_internal.h")
 FLUSH_BYTES = 256 << 20                           # > 129 MB L2
 
@@ -104,18 +104,60 @@ def profiled_traffic(variant: str, workload: str):
 
 
 class Clocks:
-    """Samples nvidia-smi every 200 ms while running."""
+    """SM clock, its maximum, power and clock-event (throttle) reasons of this process's
+    GPU, sampled DURING the timed region.
+
+    NVML (the library nvidia-smi reads) is polled from a background thread every ~2 ms,
+    so that even a region of a few milliseconds gets samples; ``nvidia-smi -lms 200`` is
+    the fallback when NVML cannot be loaded.  Only settings are read, nothing is set."""
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+    # nvmlClocksEventReason* bits (public NVML API)
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
     Q = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, uuid: str):
         self.uuid = uuid.replace("GPU-", "").lower()
+        self.samples = []
         self.proc = None
-        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.thread = None
+        self.nvml = None
+        self.dev = None
+        try:
+            import ctypes
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() == 0:
+                h = ctypes.c_void_p()
+                if nv.nvmlDeviceGetHandleByUUID(("GPU-" + self.uuid).encode(), ctypes.byref(h)) == 0:
+                    self.nvml, self.dev = nv, h
+        except OSError:
+            self.nvml = None
+
+    def _poll(self):
+        import ctypes
+        nv, h = self.nvml, self.dev
+        sm, mx, pw, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self._stop:
+            ok = nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(sm)) == 0     # NVML_CLOCK_SM
+            ok = ok and nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0
+            p_ok = nv.nvmlDeviceGetPowerUsage(h, ctypes.byref(pw)) == 0
+            r_ok = get_reasons(h, ctypes.byref(rs)) == 0
+            if ok:
+                self.samples.append((time.perf_counter(), float(sm.value), float(mx.value),
+                                     pw.value / 1e3 if p_ok else None, int(rs.value) if r_ok else 0))
+            time.sleep(0.002)
 
     def start(self):
+        self._stop = False
+        if self.nvml is not None:
+            import threading
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            return
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -123,7 +165,20 @@ class Clocks:
         except OSError:
             self.proc = None
 
-    def stop(self):
+    def stop(self, t_begin=None, t_end=None):
+        """Summary of the samples taken between t_begin and t_end (perf_counter times;
+        all samples when not given)."""
+        if self.thread is not None:
+            self._stop = True
+            self.thread.join()
+            rows = [r for r in self.samples if (t_begin is None or r[0] >= t_begin) and (t_end is None or r[0] <= t_end)]
+            if not rows:
+                return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0, "source": "nvml"}
+            pw = [r[3] for r in rows if r[3] is not None]
+            reasons = sorted({n for r in rows for n, b in self.BITS.items() if r[4] & b})
+            return {"sm_mhz": statistics.median(r[1] for r in rows), "sm_max_mhz": max(r[2] for r in rows),
+                    "power_w_median": statistics.median(pw) if pw else None, "reasons": reasons,
+                    "samples": len(rows), "source": "NVML, polled every ~2 ms during the timed region"}
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -148,7 +203,7 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
                 "power_w_median": statistics.median(pw) if pw else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "source": "nvidia-smi -lms 200"}
 
 
 DESCRIBE = {"doppler2d": "rotating-disk Doppler stand-in (Sec. 4.1 shape)",
@@ -280,8 +335,9 @@ def run_ours(args):
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     barrier()
-    t_wall = time.perf_counter() - t_wall
-    clk = clocks.stop()
+    t_end = time.perf_counter()
+    clk = clocks.stop(t_wall, t_end)
+    t_wall = t_end - t_wall
     times_ms = [a.elapsed_time(b) for a, b in ev]
     t_sum = sum(times_ms) / 1e3
     t_max = shard.max_over_ranks(t_sum)

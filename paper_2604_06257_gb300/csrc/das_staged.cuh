@@ -66,6 +66,94 @@ struct SlotMeta {
   float4 e;             // element position (sample units)
 };
 
+// ---- producer (shared by the staged kernels) --------------------------------------------
+// The producer warp evaluates 32 (element, transmit) pairs at a time (one lane each, loads
+// issued together), then lane 0 issues the copies of the usable ones in pair order: it
+// claims ring slot r % NBUF once every consumer warp has released the slot's previous use,
+// publishes (t, c, lo, rows, element) and copies the window with one bulk copy that
+// completes on the slot's "full" barrier.  Returns false when a wait gave up (the error
+// word is then set); r counts the slots issued.
+template <int NBUF>
+__device__ __forceinline__ bool produce_windows(const DasParams& p, int64_t tile, int lane, unsigned char* ring,
+                                                size_t slot_bytes, int sample_bytes, SlotMeta* meta, uint64_t* full,
+                                                uint64_t* empty, int& r) {
+  const unsigned char* iq = static_cast<const unsigned char*>(p.iq);
+  const size_t row_bytes = static_cast<size_t>(p.F) * sample_bytes;
+  const size_t slab = static_cast<size_t>(p.S) * row_bytes;
+  const float4 blo = p.tbox[2 * tile], bhi = p.tbox[2 * tile + 1];
+  const int npairs = p.C * p.T;
+  bool ok = true;
+  for (int pb = 0; pb < npairs && ok; pb += 32) {
+    const int pi = pb + lane;
+    int t = 0, c = 0, lo = 0, rows = 0;
+    float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool use = false;
+    if (pi < npairs) {
+      c = pi / p.T;
+      t = pi - c * p.T;
+      e = __ldg(&p.elem[c]);
+      use = pair_window(blo, bhi, __ldg(&p.txr[tile * p.txr_stride + t]), e, p, lo, rows);
+      rows = min(rows, p.rows_cap);
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, use);
+    while (todo) {
+      const int j = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int tj = __shfl_sync(0xffffffffu, t, j), cj = __shfl_sync(0xffffffffu, c, j);
+      const int loj = __shfl_sync(0xffffffffu, lo, j), rowsj = __shfl_sync(0xffffffffu, rows, j);
+      float4 ej;
+      ej.x = __shfl_sync(0xffffffffu, e.x, j);
+      ej.y = __shfl_sync(0xffffffffu, e.y, j);
+      ej.z = __shfl_sync(0xffffffffu, e.z, j);
+      ej.w = 0.f;
+      if (lane == 0) {
+        const int slot = r % NBUF;
+        if (r >= NBUF && !mbar_wait_bounded(&empty[slot], ((r / NBUF) - 1) & 1, p.wait_limit)) {
+          atomicOr(p.err, 1);
+          ok = false;
+        } else {
+          meta[slot].t = tj;
+          meta[slot].c = cj;
+          meta[slot].lo = loj;
+          meta[slot].rows = rowsj;
+          meta[slot].e = ej;
+          const uint32_t bytes = static_cast<uint32_t>(rowsj * row_bytes);
+          mbar_arrive_expect_tx(&full[slot], bytes);
+          if (!p.debug_stall)
+            bulk_g2s(ring + slot * slot_bytes,
+                     iq + (static_cast<size_t>(tj) * p.C + cj) * slab + static_cast<size_t>(loj) * row_bytes, bytes,
+                     &full[slot]);
+        }
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      ++r;
+    }
+  }
+  return ok;
+}
+
+// Lane 0 of the producer after its last pair: one end-of-sequence marker per pair a
+// consumer round can hold; or, when abandoning after a timeout, a bounded wait for the
+// copies already issued, so that none lands after the block has exited.
+template <int NBUF, int PB>
+__device__ __forceinline__ void finish_producer(const DasParams& p, bool ok, int r, SlotMeta* meta, uint64_t* full,
+                                                uint64_t* empty) {
+  if (ok) {
+    for (int k = 0; k < PB; ++k) {
+      const int rr = r + k, slot = rr % NBUF;
+      if (rr >= NBUF && !mbar_wait_bounded(&empty[slot], ((rr / NBUF) - 1) & 1, p.wait_limit)) {
+        atomicOr(p.err, 1);
+        break;
+      }
+      meta[slot].c = -1;
+      mbar_arrive(&full[slot]);
+    }
+  } else {
+    for (int k = max(0, r - NBUF); k < r; ++k) mbar_wait_bounded(&full[k % NBUF], (k / NBUF) & 1, p.wait_limit);
+  }
+}
+
 // MAXR: register cap per thread, chosen so that the intended number of blocks fits per SM.
 // TABLE: terms read from the plan's term table instead of evaluated on the fly.
 template <class IQ, int VEC, int NV, int FL, int VPG, int NWC, int NBUF, int MAXR, bool TABLE>
@@ -152,69 +240,9 @@ __global__ void __launch_bounds__((NWC + 1) * 32) __maxnreg__(MAXR) k_das_staged
         }
       }
     }
-    const float4 blo = p.tbox[2 * tile], bhi = p.tbox[2 * tile + 1];
-    const int npairs = TABLE ? 0 : p.C * p.T;
-    for (int pb = 0; pb < npairs && ok; pb += 32) {
-      const int pi = pb + lane;
-      int t = 0, c = 0, lo = 0, rows = 0;
-      float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
-      bool use = false;
-      if (pi < npairs) {
-        c = pi / p.T;
-        t = pi - c * p.T;
-        e = __ldg(&p.elem[c]);
-        use = pair_window(blo, bhi, __ldg(&p.txr[tile * p.txr_stride + t]), e, p, lo, rows);
-        rows = min(rows, p.rows_cap);
-      }
-      unsigned todo = __ballot_sync(0xffffffffu, use);
-      while (todo) {
-        const int j = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const int tj = __shfl_sync(0xffffffffu, t, j), cj = __shfl_sync(0xffffffffu, c, j);
-        const int loj = __shfl_sync(0xffffffffu, lo, j), rowsj = __shfl_sync(0xffffffffu, rows, j);
-        float4 ej;
-        ej.x = __shfl_sync(0xffffffffu, e.x, j);
-        ej.y = __shfl_sync(0xffffffffu, e.y, j);
-        ej.z = __shfl_sync(0xffffffffu, e.z, j);
-        ej.w = 0.f;
-        if (lane == 0) {
-          const int slot = r % NBUF;
-          if (r >= NBUF && !mbar_wait_bounded(&empty[slot], ((r / NBUF) - 1) & 1, p.wait_limit)) {
-            atomicOr(p.err, 1);
-            ok = false;
-          } else {
-            meta[slot].t = tj;
-            meta[slot].c = cj;
-            meta[slot].lo = loj;
-            meta[slot].rows = rowsj;
-            meta[slot].e = ej;
-            const uint32_t bytes = static_cast<uint32_t>(rowsj) * p.F * kBytes;
-            mbar_arrive_expect_tx(&full[slot], bytes);
-            if (!p.debug_stall)
-              bulk_g2s(ring + slot * slot_elems,
-                       iq + (static_cast<size_t>(tj) * p.C + cj) * slab + static_cast<size_t>(loj) * row_elems, bytes,
-                       &full[slot]);
-          }
-        }
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) break;
-        ++r;
-      }
-    }
-    if (lane != 0) return;
-    if (ok) {   // one end-of-sequence marker per pair a consumer round can hold
-      for (int k = 0; k < PB; ++k) {
-        const int rr = r + k, slot = rr % NBUF;
-        if (rr >= NBUF && !mbar_wait_bounded(&empty[slot], ((rr / NBUF) - 1) & 1, p.wait_limit)) {
-          atomicOr(p.err, 1);
-          break;
-        }
-        meta[slot].c = -1;
-        mbar_arrive(&full[slot]);
-      }
-    } else {    // abandoning: let the copies already issued land before the block can exit
-      for (int k = max(0, r - NBUF); k < r; ++k) mbar_wait_bounded(&full[k % NBUF], (k / NBUF) & 1, p.wait_limit);
-    }
+    if constexpr (!TABLE)
+      ok = produce_windows<NBUF>(p, tile, lane, smem, L.slot_bytes, kBytes, meta, full, empty, r);
+    if (lane == 0) finish_producer<NBUF, PB>(p, ok, r, meta, full, empty);
     return;
   }
 
@@ -304,8 +332,8 @@ __global__ void __launch_bounds__((NWC + 1) * 32) __maxnreg__(MAXR) k_das_staged
         for (int k = 0; k < VPG; ++k) {
           const float4 tr = tp[k * G + g];
           const int row = max(__float_as_int(tr.w) - lo, 0);
-          const float c1r = tr.x * tr.z, c1i = tr.y * tr.z;
-          const float c0r = tr.x - c1r, c0i = tr.y - c1i;
+          const float4 cw = tap_weights(tr);
+          const float c0r = cw.x, c0i = cw.y, c1r = cw.z, c1i = cw.w;
           gather_mac<IQ, VEC, NV, FL, true>(acc[k], win + row * row_elems, row_elems, p.F, f_base, jl, c0r, c0i, c1r,
                                             c1i);
         }
@@ -319,8 +347,8 @@ __global__ void __launch_bounds__((NWC + 1) * 32) __maxnreg__(MAXR) k_das_staged
           const float4 tr = tp[k * G + g];
           const int i0 = __float_as_int(tr.w);
           if (i0 >= 0) {
-            const float c1r = tr.x * tr.z, c1i = tr.y * tr.z;
-            const float c0r = tr.x - c1r, c0i = tr.y - c1i;
+            const float4 cw = tap_weights(tr);
+            const float c0r = cw.x, c0i = cw.y, c1r = cw.z, c1i = cw.w;
             const int row = i0 - lo;
             if (row >= 0 && row + 1 < rows)
               gather_mac<IQ, VEC, NV, FL, true>(acc[k], win + row * row_elems, row_elems, p.F, f_base, jl, c0r, c0i,

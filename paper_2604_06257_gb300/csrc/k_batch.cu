@@ -79,8 +79,8 @@ __device__ __forceinline__ void batch_frames_tile(const DasParams& p, int FL, in
             const float4 r = terms[tt * 32 + j * WV + k * G + g];
             const int i0 = __float_as_int(r.w);
             if (i0 >= 0) {
-              const float c1r = r.x * r.z, c1i = r.y * r.z;
-              const float c0r = r.x - c1r, c0i = r.y - c1i;
+              const float4 cw = tap_weights(r);
+              const float c0r = cw.x, c0i = cw.y, c1r = cw.z, c1i = cw.w;
               const IQ* row0 = base + static_cast<size_t>(i0) * p.F;
 #pragma unroll
               for (int mm = 0; mm < NV; ++mm) {
@@ -148,8 +148,8 @@ __device__ __forceinline__ void batch_channels_tile(const DasParams& p, int64_t 
         const float4 r = term_record(__ldg(&p.tx[static_cast<size_t>(t) * p.V + v]), geo, p);
         const int i0 = __float_as_int(r.w);
         if (i0 < 0) continue;
-        const float c1r = r.x * r.z, c1i = r.y * r.z;
-        const float c0r = r.x - c1r, c0i = r.y - c1i;
+        const float4 cw = tap_weights(r);
+        const float c0r = cw.x, c0i = cw.y, c1r = cw.z, c1i = cw.w;
         const IQ* row0 = iq + ((static_cast<size_t>(t) * p.C + c) * p.S + i0) * p.F;
 #pragma unroll
         for (int f = 0; f < FMAX; ++f) {

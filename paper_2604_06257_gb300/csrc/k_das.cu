@@ -105,8 +105,8 @@ __global__ void __launch_bounds__(NWARP * 32) k_das_frames(const DasParams p) {
             const float4 r = terms[tt * 32 + j * WV + k * G + g];
             const int i0 = __float_as_int(r.w);
             if (i0 >= 0) {
-              const float c1r = r.x * r.z, c1i = r.y * r.z;
-              const float c0r = r.x - c1r, c0i = r.y - c1i;
+              const float4 cw = tap_weights(r);
+              const float c0r = cw.x, c0i = cw.y, c1r = cw.z, c1i = cw.w;
               gather_mac<IQ, VEC, NV, FL, false>(acc[k], base + static_cast<size_t>(i0) * row_elems, row_elems, p.F,
                                                  f_base, jl, c0r, c0i, c1r, c1i);
             }
@@ -166,8 +166,8 @@ __global__ void __launch_bounds__(NWARP * 32) k_das_channels(const DasParams p) 
         const float4 r = term_record(__ldg(&p.tx[static_cast<size_t>(t) * p.V + v]), geo, p);
         const int i0 = __float_as_int(r.w);
         if (i0 < 0) continue;
-        const float c1r = r.x * r.z, c1i = r.y * r.z;
-        const float c0r = r.x - c1r, c0i = r.y - c1i;
+        const float4 cw = tap_weights(r);
+        const float c0r = cw.x, c0i = cw.y, c1r = cw.z, c1i = cw.w;
         const IQ* row0 = iq + ((static_cast<size_t>(t) * p.C + c) * p.S + i0) * p.F;
 #pragma unroll
         for (int f = 0; f < FMAX; ++f) {
@@ -249,6 +249,23 @@ const VariantShape kShapes[V_COUNT] = {
     {"staged_b16_ft32_v4",         4,  8,  16,   32,  kWarps, false, true,  4, 4, 2},
     {"staged_c64p_ft32_v4w7",      4,  8,  16,   32,  7,      false, true,  4, 8, 3, 8},
     {"staged_c64_ft32_v4w7",       4,  8,  16,   32,  7,      false, true,  4, 8, 0, 8},
+    {"staged_c64p_x32_v4w7",       4,  8,  16,   32,  7,      false, true,  4, 8, 3, 8, true},
+    {"staged_c64p_x64_v4",         4, 16,   8,   64,  kWarps, false, true,  8, 8, 3, 0, true},
+    {"staged_c64p_x32_f4v2w7",     4,  8,   8,   32,  7,      false, true,  8, 8, 3, 4, true},
+    {"staged_c64p_x32_f8v1w7",     8,  4,   8,   32,  7,      false, true,  8, 8, 3, 4, true},
+    {"staged_c64p_x32_f4v2w15",    4,  8,   8,   32,  15,     false, true,  8, 8, 3, 8, true},
+    {"staged_c64p_x32_f8v1w15",    8,  4,   8,   32,  15,     false, true,  8, 8, 3, 8, true},
+    {"staged_c64p_x64_f8v2",       8,  8,   8,   64,  kWarps, false, true,  8, 8, 3, 0, true},
+    {"staged_c64p_x32_f8v1w15t24", 8,  4,   8,   32,  15,     false, true,  8, 8, 3, 24, true},
+    {"staged_c64p_x32_f8v1w15t40", 8,  4,   8,   32,  15,     false, true,  8, 8, 3, 40, true},
+    {"staged_c64p_x32_f8v1w15t24s",8,  4,   8,   32,  15,     false, true,  8, 8, 3, 24, true},
+    {"staged_c64p_x64_v4s",        4, 16,   8,   64,  kWarps, false, true,  8, 8, 3, 0, true},
+    {"staged_c64p_x32_f8v1w7t14",  8,  4,   8,   32,  7,      false, true,  8, 8, 3, 14, true},
+    {"staged_c64p_x32_f8v1w7t14e", 8,  4,   8,   32,  7,      false, true,  8, 8, 3, 14, true},
+    {"staged_c64p_x32_f4v2w7t14",  4,  8,   8,   32,  7,      false, true,  8, 8, 3, 14, true},
+    {"staged_c64p_x32_f8v1w15t30r12",  8, 4, 8,  32,  15,     false, true, 12, 8, 3, 30, true},
+    {"staged_c64p_x32_f8v1w15t30r12e", 8, 4, 8,  32,  15,     false, true, 12, 8, 3, 30, true},
+    {"staged_c64p_x64_v4e",        4, 16,   8,   64,  kWarps, false, true,  8, 8, 3, 0, true},
 };
 
 template <class K>

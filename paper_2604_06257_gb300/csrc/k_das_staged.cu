@@ -105,11 +105,13 @@ cudaError_t launch_tile_bounds(const DasParams& p, float4* tbox, float2* txr, in
 // ---- dispatch ------------------------------------------------------------------------------
 size_t staged_smem_bytes(Variant v, int rows_cap, int F, int T, bool table) {
   const VariantShape& sh = variant_shape(v);
+  if (sh.exact_frames) return exact_smem_bytes(v, rows_cap, T);
   if (sh.ring_slots == 8) return RingLayout<8>(rows_cap, F, sh.iq_bytes, T, sh.warps, sh.voxels_per_warp, table).total();
   return RingLayout<kRing>(rows_cap, F, sh.iq_bytes, T, sh.warps, sh.voxels_per_warp, table).total();
 }
 
 cudaError_t launch_das_staged(const DasParams& p, Variant v, cudaStream_t s) {
+  if (variant_shape(v).exact_frames) return launch_das_exact(p, v, s);
   const size_t sm = staged_smem_bytes(v, p.rows_cap, p.F, p.T, false);
   switch (v) {
     case V_ST32_C64: return go_staged(k_das_staged<float2, 2, 2, 8, 8, 8, kRing, 112, false>, 8, p, sm, s);

@@ -46,6 +46,23 @@ enum Variant : int32_t {
   V_ST32_B16_V4,     // staged, 32-frame tile, bfloat16 pairs, 4 voxels per lane group
   V_ST32_C64P_V4W7,  // staged, split rows, 7 consumer warps, 64 registers: 4 blocks per SM
   V_ST32_C64_V4W7,   // staged, interleaved, 7 consumer warps, 64 registers: 4 blocks per SM
+  V_SX32_C64P,       // staged, split rows, F = 32 exactly (compile-time frames), 7 consumer warps
+  V_SX64_C64P,       // staged, split rows, F = 64 exactly (compile-time frames), 8 consumer warps
+  V_SX32_F4V2W7,     // F = 32 exactly: 4 frames x 2 voxels per lane, 7 consumer warps
+  V_SX32_F8V1W7,     // F = 32 exactly: 8 frames x 1 voxel per lane, 7 consumer warps
+  V_SX32_F4V2W15,    // F = 32 exactly: 4 frames x 2 voxels per lane, 15 consumer warps
+  V_SX32_F8V1W15,    // F = 32 exactly: 8 frames x 1 voxel per lane, 15 consumer warps
+  V_SX64_F8V2,       // F = 64 exactly: 8 frames x 2 voxels per lane, 8 consumer warps
+  V_SX32_F8V1W15T24, // as V_SX32_F8V1W15 with 24 x 5 voxel tiles (2D)
+  V_SX32_F8V1W15T40, // as V_SX32_F8V1W15 with 40 x 3 voxel tiles (2D)
+  V_SX32_F8V1W15T24S,// as V_SX32_F8V1W15T24, consumers suspended in hardware while waiting
+  V_SX64_C64PS,      // as V_SX64_C64P, consumers suspended in hardware while waiting
+  V_SX32_F8V1W7T14,  // F = 32: 8 frames x 1 voxel per lane, 7 consumer warps, 14 x 4 tiles
+  V_SX32_F8V1W7T14E, // as V_SX32_F8V1W7T14, ring slots released per pair
+  V_SX32_F4V2W7T14,  // F = 32: 4 frames x 2 voxels per lane, 7 consumer warps, 14 x 4 tiles
+  V_SX32_F8V1W15T30R12,  // F = 32: 8 frames x 1 voxel, 15 consumer warps, 30 x 4 tiles, 12 slots
+  V_SX32_F8V1W15T30R12E, // as V_SX32_F8V1W15T30R12, ring slots released per pair
+  V_SX64_C64PE,      // as V_SX64_C64P, ring slots released per pair
   V_COUNT
 };
 
@@ -62,6 +79,7 @@ struct VariantShape {
   int iq_bytes;          // bytes per complex sample
   int iq_type;           // mach_iq_dtype the variant reads
   int tile2d_x;          // 2D tile width (0: squarest power-of-two split)
+  bool exact_frames;     // serves only F == frame_tile (k_das_exact.cu)
 };
 
 const VariantShape& variant_shape(Variant v);
@@ -132,6 +150,9 @@ cudaError_t launch_tile_bounds(const DasParams& p, float4* tbox, float2* txr, in
                                cudaStream_t s);
 size_t staged_smem_bytes(Variant v, int rows_cap, int F, int T, bool table);
 cudaError_t launch_das_staged(const DasParams& p, Variant v, cudaStream_t s);
+// Staged variants whose frame count is a compile-time constant (k_das_exact.cu).
+size_t exact_smem_bytes(Variant v, int rows_cap, int T);
+cudaError_t launch_das_exact(const DasParams& p, Variant v, cudaStream_t s);
 // Plan-time term table (k_das_table.cu): which staged variants have a table form, the
 // per-(tile, element) windows of every transmit (rows 0 = pair not used) and their
 // count, the pair list and records, and the table-mode launch.

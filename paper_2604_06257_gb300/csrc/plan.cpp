@@ -130,6 +130,8 @@ Variant pick_variant(int iq_dtype, int F) {
     return V_S32_C64;
   }
   if (iq_dtype == MACH_IQ_C64_SPLIT) {   // F % 4 == 0 and F > 4 (checked by validate)
+    if (F == 32) return V_SX32_F8V1W7T14E;
+    if (F == 64) return V_SX64_C64P;
     if (F <= 16) return V_F32_C64P;
     if (F <= 32) return V_ST32_C64P_V4W7;
     if (F <= 64) return V_ST64_C64P_V4;
@@ -164,8 +166,13 @@ Variant unstaged(Variant v) {
     case V_ST32_H16: case V_ST32_H16_V4: return V_F32_H16;
     case V_ST64_H16: case V_ST64_H16_V4: return V_F64_H16;
     case V_ST32_B16: case V_ST32_B16_V4: return V_F32_B16;
-    case V_ST32_C64P_V4: case V_ST32_C64P_V4W7: return V_F32_C64P;
-    case V_ST64_C64P_V4: return V_F64_C64P;
+    case V_ST32_C64P_V4: case V_ST32_C64P_V4W7: case V_SX32_C64P: case V_SX32_F4V2W7: case V_SX32_F8V1W7:
+    case V_SX32_F4V2W15: case V_SX32_F8V1W15: case V_SX32_F8V1W15T24: case V_SX32_F8V1W15T40:
+    case V_SX32_F8V1W15T24S: case V_SX32_F8V1W7T14: case V_SX32_F8V1W7T14E: case V_SX32_F4V2W7T14:
+    case V_SX32_F8V1W15T30R12: case V_SX32_F8V1W15T30R12E:
+      return V_F32_C64P;
+    case V_ST64_C64P_V4: case V_SX64_C64P: case V_SX64_F8V2: case V_SX64_C64PS: case V_SX64_C64PE:
+      return V_F64_C64P;
     case V_ST64_B16_V4: return V_F64_B16;
     default: return v;
   }
@@ -178,7 +185,35 @@ bool variant_accepts(Variant v, int iq_dtype, int F) {
   const int vec = s.frames_per_lane == 1 ? 1 : (s.iq_type == MACH_IQ_C64 ? 2 : 4);
   if (F % vec != 0) return false;
   if (s.staged && F > s.frame_tile) return false;
+  if (s.exact_frames && F != s.frame_tile) return false;
   return true;
+}
+
+// The variant to try when a staged variant's ring does not fit in shared memory: one with
+// fewer ring slots (the variant itself when there is none).
+Variant staged_fallback(Variant v) {
+  switch (v) {
+    case V_ST64_C64_V4: return V_ST64_C64;
+    case V_ST64_H16_V4: return V_ST64_H16;
+    case V_SX32_F8V1W15: case V_SX32_F4V2W15: case V_SX32_F8V1W7: case V_SX32_F4V2W7: case V_SX32_F8V1W15T24:
+    case V_SX32_F8V1W15T40: case V_SX32_F8V1W15T24S: case V_SX32_F8V1W7T14: case V_SX32_F8V1W7T14E:
+    case V_SX32_F4V2W7T14: case V_SX32_F8V1W15T30R12: case V_SX32_F8V1W15T30R12E:
+      return V_SX32_C64P;
+    default: return v;
+  }
+}
+
+// The generic staged variant an exact-frame variant specialises (term tables are built
+// for the generic kernels' record layout).
+Variant generic_staged(Variant v) {
+  switch (v) {
+    case V_SX32_C64P: case V_SX32_F4V2W7: case V_SX32_F8V1W7: case V_SX32_F4V2W15: case V_SX32_F8V1W15:
+    case V_SX32_F8V1W15T24: case V_SX32_F8V1W15T40: case V_SX32_F8V1W15T24S: case V_SX32_F8V1W7T14:
+    case V_SX32_F8V1W7T14E: case V_SX32_F4V2W7T14: case V_SX32_F8V1W15T30R12: case V_SX32_F8V1W15T30R12E:
+      return V_ST32_C64P_V4W7;
+    case V_SX64_C64P: case V_SX64_F8V2: case V_SX64_C64PS: case V_SX64_C64PE: return V_ST64_C64P_V4;
+    default: return v;
+  }
 }
 
 // Voxel tile of one block: compact boxes so that the voxels sharing a block (and the
@@ -273,7 +308,7 @@ static mach_status configure_tiles(DasParams& b, Variant var, bool list, int64_t
     // candidate blocks, most compact first; the first one that divides the tile is used
     static const int c2d32[][3] = {{8, 1, 4}, {16, 1, 2}, {4, 1, 8}};
     static const int c2d16[][3] = {{4, 1, 4}, {8, 1, 2}, {16, 1, 1}};
-    static const int c2d8[][3] = {{4, 1, 2}, {8, 1, 1}};
+    static const int c2d8[][3] = {{4, 1, 2}, {8, 1, 1}, {2, 1, 4}};
     static const int c3d32[][3] = {{4, 4, 2}, {8, 4, 1}};
     static const int c3d16[][3] = {{4, 4, 1}, {8, 2, 1}};
     static const int c3d8[][3] = {{4, 2, 1}, {8, 1, 1}};
@@ -281,7 +316,7 @@ static mach_status configure_tiles(DasParams& b, Variant var, bool list, int64_t
     const int(*cand)[3] = nullptr;
     int nc = 0;
     if (b.ny == 1) {
-      if (wv == 32) { cand = c2d32; nc = 3; } else if (wv == 16) { cand = c2d16; nc = 3; } else if (wv == 8) { cand = c2d8; nc = 2; }
+      if (wv == 32) { cand = c2d32; nc = 3; } else if (wv == 16) { cand = c2d16; nc = 3; } else if (wv == 8) { cand = c2d8; nc = 3; }
     } else {
       if (wv == 32) { cand = c3d32; nc = 2; } else if (wv == 16) { cand = c3d16; nc = 2; } else if (wv == 8) { cand = c3d8; nc = 2; }
     }
@@ -376,6 +411,7 @@ mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) 
                          : static_cast<int64_t>(d->grid_dims[0]) * d->grid_dims[1] * d->grid_dims[2];
   if (list && V > INT32_MAX) return MACH_ERR_UNSUPPORTED;
   Variant var = pick_variant(d->iq_dtype, F);
+  if (d->term_table) var = generic_staged(var);
   const bool forced = g_force_variant >= 0;
   if (forced) {
     if (g_force_variant >= V_COUNT || !variant_accepts(static_cast<Variant>(g_force_variant), d->iq_dtype, F))
@@ -512,49 +548,56 @@ mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) 
   b.debug_stall = g_stall;
 
   if (variant_shape(var).staged) {
-    // per-tile bounds, ring size, and the number of windows one run copies
-    if ((st = dev_alloc(reinterpret_cast<void**>(&p->d_tbox), sizeof(float4) * 2 * tiles0, &p->device_bytes)) != MACH_OK)
+    // per-tile bounds, ring size, and the number of windows one run copies.  When the
+    // chosen variant's ring does not fit, variants with fewer ring slots are tried in turn
+    // (their tiles differ, so each gets its own bounds), and last the L1-path variant.
+    const bool tab = d->term_table != 0;
+    Variant chain[4];
+    int nchain = 0;
+    chain[nchain++] = var;
+    if (!forced)
+      for (Variant f = staged_fallback(var); f != chain[nchain - 1] && nchain < 4; f = staged_fallback(f))
+        chain[nchain++] = f;
+    int64_t tiles_max = tiles0;
+    for (int k = 1; k < nchain; ++k) {
+      DasParams tmp = b;
+      if ((st = configure_tiles(tmp, chain[k], list, V, F)) != MACH_OK) return fail(st);
+      tiles_max = std::max<int64_t>(tiles_max, static_cast<int64_t>(tmp.tiles_x) * tmp.tiles_y * tmp.tiles_z);
+    }
+    if ((st = dev_alloc(reinterpret_cast<void**>(&p->d_tbox), sizeof(float4) * 2 * tiles_max, &p->device_bytes)) != MACH_OK)
       return fail(st);
-    if ((st = dev_alloc(reinterpret_cast<void**>(&p->d_txr), sizeof(float2) * T * tiles0, &p->device_bytes)) != MACH_OK)
+    if ((st = dev_alloc(reinterpret_cast<void**>(&p->d_txr), sizeof(float2) * T * tiles_max, &p->device_bytes)) != MACH_OK)
       return fail(st);
     if ((st = dev_alloc(reinterpret_cast<void**>(&d_stats), 2 * sizeof(int), &scratch_bytes)) != MACH_OK) return fail(st);
-    if (launch_tile_bounds(b, p->d_tbox, p->d_txr, d_stats, s) != cudaSuccess) return fail(MACH_ERR_CUDA);
-    int stats[2] = {0, 0};
-    if (cudaMemcpyAsync(stats, d_stats, sizeof(stats), cudaMemcpyDeviceToHost, s) != cudaSuccess) return fail(MACH_ERR_CUDA);
-    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(MACH_ERR_CUDA);
-    p->rows_cap = std::max(2, stats[0]);
-    p->copy_pairs = stats[1];
     b.tbox = p->d_tbox;
     b.txr = p->d_txr;
-    b.rows_cap = p->rows_cap;
-    const bool tab = d->term_table != 0;
-    const Variant smaller_ring = var == V_ST64_C64_V4 ? V_ST64_C64 : (var == V_ST64_H16_V4 ? V_ST64_H16 : var);
-    if (!forced && smaller_ring != var && staged_smem_bytes(var, p->rows_cap, F, T, tab) > kStagedSmemCap &&
-        staged_smem_bytes(smaller_ring, p->rows_cap, F, T, tab) <= kStagedSmemCap) {
-      // an 8-slot ring does not fit: the 2-pair variant needs only 4 slots (its tiles are
-      // larger, so recompute them and their bounds)
-      var = smaller_ring;
-      p->variant = var;
-      if ((st = configure_tiles(b, var, list, V, F)) != MACH_OK) return fail(st);
-      const int64_t tiles1 = static_cast<int64_t>(b.tiles_x) * b.tiles_y * b.tiles_z;
-      if (tiles1 > tiles0) return fail(MACH_ERR_UNSUPPORTED);   // (larger tiles: never more of them)
+    bool fits = false;
+    for (int k = 0; k < nchain && !fits; ++k) {
+      if (k > 0) {
+        var = chain[k];
+        p->variant = var;
+        if ((st = configure_tiles(b, var, list, V, F)) != MACH_OK) return fail(st);
+      }
       if (launch_tile_bounds(b, p->d_tbox, p->d_txr, d_stats, s) != cudaSuccess) return fail(MACH_ERR_CUDA);
-      if (cudaMemcpyAsync(stats, d_stats, sizeof(stats), cudaMemcpyDeviceToHost, s) != cudaSuccess) return fail(MACH_ERR_CUDA);
+      int stats[2] = {0, 0};
+      if (cudaMemcpyAsync(stats, d_stats, sizeof(stats), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return fail(MACH_ERR_CUDA);
       if (cudaStreamSynchronize(s) != cudaSuccess) return fail(MACH_ERR_CUDA);
       p->rows_cap = std::max(2, stats[0]);
       p->copy_pairs = stats[1];
       b.rows_cap = p->rows_cap;
+      fits = staged_smem_bytes(var, p->rows_cap, F, T, tab) <= kStagedSmemCap;
     }
-    if (staged_smem_bytes(var, p->rows_cap, F, T, tab) > kStagedSmemCap) {
+    if (!fits) {
       if (forced || tab) return fail(MACH_ERR_UNSUPPORTED);
-      // the tiles' windows are too long for the ring: use the L1-cached variant
+      // the tiles' windows are too long for any ring: use the L1-cached variant
       cudaFree(p->d_tbox);
       cudaFree(p->d_txr);
       p->d_tbox = nullptr;
       p->d_txr = nullptr;
       b.tbox = nullptr;
       b.txr = nullptr;
-      p->device_bytes -= static_cast<int64_t>(sizeof(float4) * 2 * tiles0 + sizeof(float2) * T * tiles0);
+      p->device_bytes -= static_cast<int64_t>(sizeof(float4) * 2 * tiles_max + sizeof(float2) * T * tiles_max);
       var = unstaged(var);
       p->variant = var;
       p->rows_cap = 0;

@@ -83,6 +83,14 @@ __device__ __forceinline__ void load_vec(const IQ* p, float2 (&o)[VEC]) {
   }
 }
 
+// Complex tap weights of a term record (a cos phi, a sin phi, w, .): c1 = w c and
+// c0 = c - c1, each product and difference rounded on its own (never contracted into an
+// FMA), so that every kernel derives the same bits from the same record.
+__device__ __forceinline__ float4 tap_weights(const float4 r) {
+  const float c1r = __fmul_rn(r.x, r.z), c1i = __fmul_rn(r.y, r.z);
+  return make_float4(__fsub_rn(r.x, c1r), __fsub_rn(r.y, c1i), c1r, c1i);
+}
+
 __device__ __forceinline__ void mac1(float2& acc, float c0r, float c0i, float c1r, float c1i, float2 x0, float2 x1) {
   acc.x = fmaf(c0r, x0.x, acc.x);
   acc.x = fmaf(-c0i, x0.y, acc.x);

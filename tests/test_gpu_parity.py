@@ -360,6 +360,8 @@ STAGED_CASES = [
     ("staged_b16_ft64_v4", "frames_b16_ft64", "volume3d", "bf16x2"),
     ("staged_c64p_ft32_v4", "frames_c64p_ft32", "doppler2d", "c64split"),
     ("staged_c64p_ft64_v4", "frames_c64p_ft64", "volume3d", "c64split"),
+    ("staged_c64p_x32_v4w7", "frames_c64p_ft32", "doppler2d", "c64split"),
+    ("staged_c64p_x64_v4", "frames_c64p_ft64", "volume3d", "c64split"),
     ("staged_f16_ft32_v4", "frames_f16_ft32", "doppler2d", "f16x2"),
     ("staged_b16_ft32_v4", "frames_b16_ft32", "doppler2d", "bf16x2"),
 ]
