@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--iq-dtype", default="c64split", choices=["c64", "f16x2", "bf16x2", "c64split"],
                     help="IQ storage the timed kernel reads (prepared by K0 outside the timed region)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other workloads (volume3d, bmode2d, ragged batch) reported beside the headline")
+    ap.add_argument("--sweep-axes", default="voxels,channels,frames", help="axes of --workload sweep")
     return ap.parse_args()
 
 
@@ -276,6 +279,149 @@ def count_active_terms(plan, V, C, T, chunk_terms=1 << 26):
     return total
 
 
+def active_fraction_sampled(plan, acq, n=2048, seed=0):
+    """Share of terms (voxel, element, transmit) inside the aperture and the sample range,
+    estimated on n evenly spread voxels (mach_das_terms, indices only)."""
+    import numpy as np
+    import torch
+    import paper_2604_06257_gb300 as m
+    V, C, T = acq.n_vox, acq.n_elem, acq.n_tx
+    n = min(n, V)
+    idx = torch.as_tensor(np.linspace(0, V - 1, n).astype(np.int64), device="cuda")
+    i0 = torch.empty(n * C * T, dtype=torch.int32, device="cuda")
+    m.mach_das_terms(plan.handle, idx, i0=i0)
+    return float((i0 >= 0).sum().item()) / (n * C * T)
+
+
+def time_plan(plan, iq, pd, y, steps, warmup, flush, stream):
+    """Mean device time of one mach_power_doppler call (CUDA events on the launching
+    stream, L2 flushed before every call, outside the events)."""
+    import torch
+    import paper_2604_06257_gb300 as m
+    for _ in range(warmup):
+        flush.zero_()
+        m.mach_power_doppler(plan.handle, iq, pd, y)
+    evs = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        m.mach_power_doppler(plan.handle, iq, pd, y)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in evs) / 1e3
+
+
+def peaks_and_units():
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = props.multi_processor_count
+    return {"n_sm": n_sm, "sm_max": sm_max, "fp32_tflops": n_sm * 128 * 2 * sm_max * 1e6 / 1e12,
+            "lds_gbs": n_sm * 128 * sm_max * 1e6 / 1e9, "hbm_gbs": float(peaks.get("hbm_gbs", 6800.0))}
+
+
+def oracle_error(acq, iq_c64, y, pd, n_vox, iq_ref=None):
+    """Part of the CPU baseline leg: NRMSE (dB) of the GPU frames and Power Doppler against
+    the oracle on n_vox evenly spread voxels, with the plan's float32 delay contract and
+    with exact (all-FP64) delays."""
+    import numpy as np
+    import torch
+    import oracle
+    V = acq.n_vox
+    idx = np.unique(np.linspace(0, V - 1, n_vox).astype(np.int64))
+    sel = torch.as_tensor(idx, device=y.device)
+    ys, ps = y[sel].cpu().numpy().astype(np.complex128), pd[sel].cpu().numpy().astype(np.float64)
+    ref = iq_c64.cpu() if iq_ref is None else iq_ref
+    err = {"voxels": len(idx)}
+    for mode in ("contract", "exact"):
+        yr, pr = oracle.das(acq.replace(iq_dtype="c64"), ref, idx, mode=mode)
+        err[mode] = {"frames_db": float(20 * np.log10(np.linalg.norm(ys - yr) / np.linalg.norm(yr))),
+                     "pd_db": float(20 * np.log10(np.linalg.norm(ps - pr) / np.linalg.norm(pr)))}
+    return err
+
+
+def das_leg(acq, iq_c64, dt, steps, warmup, flush, stream, cpu_check=True, err_voxels=256):
+    """One DAS + Power Doppler workload: points/s and roofline fractions; with the CPU
+    baseline leg enabled, also the error of the timed output against the oracle."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2604_06257_gb300 as m
+    a = acq.replace(iq_dtype=dt)
+    x = synth.iqmod.to_storage(iq_c64, dt)
+    V, F = a.n_vox, a.n_frames
+    with m.Plan(**m.plan_kwargs(a)) as plan:
+        info = plan.info()
+        pd = torch.empty(V, dtype=torch.float32, device="cuda")
+        y = torch.empty((V, F), dtype=torch.complex64, device="cuda")
+        t = time_plan(plan, x, pd, y, steps, warmup, flush, stream)
+        act = active_fraction_sampled(plan, a)
+    pk = peaks_and_units()
+    tf = act * a.n_elem * a.n_tx * V * F                      # active term-frames (estimated)
+    bpt = 16 if dt in ("c64", "c64split") else 8
+    out = {"value": a.points / t, "unit": UNIT, "ms_per_step": t * 1e3, "steps": steps, "warmup": warmup,
+           "variant": info["variant"], "tile": info["tile"], "dtype": dt,
+           "config": {"workload": a.name, "voxels": V, "channels": a.n_elem, "transmits": a.n_tx, "frames": F,
+                      "samples": a.n_samples, "points_per_step": a.points},
+           "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": 16 * tf / t / 1e12, "peak": pk["fp32_tflops"],
+                        "frac": 16 * tf / t / 1e12 / pk["fp32_tflops"],
+                        "sm_load_path_frac": bpt * tf / t / 1e9 / pk["lds_gbs"],
+                        "active_fraction": act, "active_fraction_source": "2048 evenly spread voxels"}}
+    if cpu_check:
+        ref = synth.iqmod.from_storage(x.cpu()) if dt in ("f16x2", "bf16x2") else None
+        out["error_db_vs_oracle"] = oracle_error(a, iq_c64, y, pd, err_voxels, ref)
+    return out
+
+
+def ragged_leg(args, flush, steps=3):
+    """The 64-instance ragged batch (float16 IQ) in one persistent launch replayed from a
+    CUDA graph, default tile shapes."""
+    import torch
+    import synth
+    from synth.ragged import ragged_instances
+    import paper_2604_06257_gb300 as m
+    acqs = ragged_instances(n=args.ragged_n, seed=4, iq_dtype="f16x2", scale=args.ragged_scale)
+    kws = [m.plan_kwargs(a) for a in acqs]
+    iqs, ys, pds = [], [], []
+    for i, a in enumerate(acqs):
+        iqs.append(synth.iqmod.to_f16x2(synth.random_iq(a, 1000 + i, device="cuda")))
+        ys.append(torch.empty((a.n_vox, a.n_frames), dtype=torch.complex64, device="cuda"))
+        pds.append(torch.empty(a.n_vox, dtype=torch.float32, device="cuda"))
+    points = sum(a.points for a in acqs)
+    with m.Batch(kws) as b:
+        b.bind(iqs, ys, pds)
+        b.run()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            b.run()
+        for _ in range(2):
+            g.replay()
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        t = statistics.mean(a.elapsed_time(b_) for a, b_ in evs) / 1e3
+        info = {k: v for k, v in b.info().items() if k != "shapes"}
+    del iqs
+    return {"value": points / t, "unit": UNIT, "ms_per_step": t * 1e3, "steps": steps,
+            "config": {"workload": f"{len(acqs)} seeded instances (seed 4, 2D and 3D, 1-48 frames, 1-15 transmits, "
+                                   "float16 IQ), one persistent launch replayed from a CUDA graph, default tile shapes",
+                       "points_per_step": points}, "batch": info}
+
+
 # ---------------------------------------------------------------- our arm ----
 
 def run_ours(args):
@@ -490,9 +636,27 @@ def run_ours(args):
                "sequential": {"value": world * acq.points * K / ts, "unit": UNIT,
                               "api": "mach_iq_convert + mach_power_doppler per call, synchronised"}}
 
-    cpu = None
+    # the CPU baseline leg: the oracle timed on a bounded sample, and the timed output
+    # checked against it on sampled voxels (contract and exact, all-FP64, delays)
+    cpu = err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(acq, iq_c64.cpu(), args.cpu_seconds)
+        m.mach_power_doppler(plan.handle, iq, pd, y)
+        err = oracle_error(acq, iq_c64, y, pd, 1024)
+
+    # the other workloads, each in its own timed region on the same GPU (rank 0, one GPU):
+    # the largest single-GPU configuration (the 128^3 matrix-array volume), the one-frame
+    # B-mode configuration and the ragged batch
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extra:
+        del iq_c64
+        for name, dt, st in (("volume3d", "c64split", 5), ("bmode2d", "c64", 300)):
+            a2, iq2 = synth.make(name, "full", device=dev)
+            extra[name] = das_leg(a2, iq2, dt, st, 3, flush, stream, cpu_check=not args.no_cpu_baseline)
+            del iq2
+            torch.cuda.empty_cache()
+        extra["ragged"] = ragged_leg(args, flush)
+        torch.cuda.empty_cache()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -511,6 +675,7 @@ def run_ours(args):
                                                            "hybrid: transmit table + receive delays on the fly"),
                                                 "active_fraction": active_terms / (V * acq.n_elem * acq.n_tx)}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "plan": info, "k0_iq_convert": k0,
+                "error_db_vs_oracle": err, "workloads": extra,
                 "other_layouts": alt,
                 "gpu_launches": launches_per_step * args.steps,
                 "clocks": clk, "wall_s_timed_region": t_wall,
@@ -790,6 +955,65 @@ def run_learned(args):
     pf.close()
 
 
+# ------------------------------------------------------------ scaling sweep ----
+
+def run_sweep(args):
+    """Throughput against voxels, channels and frames (the scaling study of Sec. 4.6,
+    Fig. 5), one JSON line per point, on the 2D Doppler geometry (one 0-degree plane wave,
+    fc 5.2 MHz, fs 20.8 MHz, 2048 samples, F# 1.0) with seeded random IQ (the values do not
+    change the work):
+      voxels   63 k - 6.3 M: the same 25.6 x 25.6 mm field of view sampled by n x n pixels;
+      channels 128 - 8192: the same 38.4 mm linear aperture with C elements (pitch 38.4 mm / C),
+               so each voxel keeps the same share of active elements;
+      frames   1 - 512: the 256 x 256 grid, 128 elements.
+    Split complex64 rows where F is a multiple of 4 above 4, interleaved complex64 otherwise;
+    the plan's default kernel for each point."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2604_06257_gb300 as m
+    from paper_2604_06257_gb300 import build as pkg_build
+    from synth.acquisition import linear_array
+
+    pkg_build.build()
+    m.lib()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    base = synth.doppler2d()
+    fov = 25.6e-3
+
+    def point(axis, value, acq):
+        F = acq.n_frames
+        dt = "c64split" if F % 4 == 0 and F > 4 else "c64"
+        iq = synth.random_iq(acq, 7, device="cuda")
+        est = 2e-12 * acq.points + 2e-5                       # rough seconds per step
+        steps = int(min(500, max(3, 0.5 / est)))
+        leg = das_leg(acq, iq, dt, steps, 3, flush, stream, cpu_check=False)
+        del iq
+        torch.cuda.empty_cache()
+        line = {"metric": METRIC, "sweep": axis, axis: value, "value": leg["value"], "unit": UNIT,
+                "ms_per_step": leg["ms_per_step"], "steps": steps, "variant": leg["variant"], "dtype": dt,
+                "higher_is_better": True, "data": "synthetic", "config": leg["config"],
+                "roofline": leg["roofline"]}
+        print(json.dumps(line), flush=True)
+
+    axes = args.sweep_axes.split(",")
+    if "voxels" in axes:
+        for n in (251, 512, 1024, 1448, 2048, 2510):
+            step = fov / n
+            acq = base.replace(grid_dims=(n, 1, n), grid_origin=(-(n - 1) * step / 2, 0.0, 10e-3),
+                               grid_step=(step, 0.0, step), name=f"sweep_vox{n * n}")
+            point("voxels", n * n, acq)
+    if "channels" in axes:
+        for C in (128, 256, 512, 1024, 2048, 4096, 8192):
+            acq = base.replace(elem_pos=linear_array(C, pitch=38.4e-3 / C), name=f"sweep_ch{C}")
+            point("channels", C, acq)
+    if "frames" in axes:
+        for F in (1, 2, 4, 8, 16, 32, 64, 128, 256, 512):
+            acq = base.replace(n_frames=F, name=f"sweep_f{F}")
+            point("frames", F, acq)
+
+
 # ---------------------------------------------------------- reference arm ----
 
 def run_reference(args):
@@ -928,6 +1152,8 @@ def main():
         run_learned(args)
     elif args.workload == "rf2d":
         run_rf(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_ours(args)
     try:
