@@ -402,7 +402,7 @@ cudaError_t go_staged(K kernel, int nwc, const DasParams& p, size_t smem, cudaSt
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const int64_t tiles = static_cast<int64_t>(p.tiles_x) * p.tiles_y * p.tiles_z;
-  kernel<<<dim3(static_cast<unsigned>(tiles), 1), (nwc + 1) * 32, smem, s>>>(p);
+  kernel<<<dim3(static_cast<unsigned>(tiles), static_cast<unsigned>(p.frame_tiles)), (nwc + 1) * 32, smem, s>>>(p);
   return cudaGetLastError();
 }
 

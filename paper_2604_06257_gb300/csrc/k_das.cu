@@ -266,6 +266,9 @@ const VariantShape kShapes[V_COUNT] = {
     {"staged_c64p_x32_f8v1w15t30r12",  8, 4, 8,  32,  15,     false, true, 12, 8, 3, 30, true},
     {"staged_c64p_x32_f8v1w15t30r12e", 8, 4, 8,  32,  15,     false, true, 12, 8, 3, 30, true},
     {"staged_c64p_x64_v4e",        4, 16,   8,   64,  kWarps, false, true,  8, 8, 3, 0, true},
+    {"staged_c64p_x16_f4v2w7",     4,  4,  16,   16,  7,      false, true,  8, 8, 3, 28, true},
+    {"staged_c64p_x16_f4v1w7",     4,  4,   8,   16,  7,      false, true,  8, 8, 3, 14, true},
+    {"staged_c64p_x8_f4v1w7",      4,  2,  16,    8,  7,      false, true,  8, 8, 3, 28, true},
 };
 
 template <class K>
@@ -284,10 +287,10 @@ size_t das_smem_bytes(Variant v) {
 }
 
 cudaError_t launch_das(const DasParams& p, Variant v, cudaStream_t s) {
-  if (kShapes[v].staged) return launch_das_staged(p, v, s);
   const size_t sm = das_smem_bytes(v);
   cudaError_t e;
-  switch (v) {
+  switch (kShapes[v].staged ? V_COUNT : v) {
+    case V_COUNT: e = launch_das_staged(p, v, s); break;
     case V_CH_C64: e = go(k_das_channels<float2, 8, 4, kWarps>, p, sm, s); break;
     case V_F16_C64: e = go(k_das_frames<float2, 2, 1, 8, 8, kWarps>, p, sm, s); break;
     case V_F32_C64: e = go(k_das_frames<float2, 2, 2, 8, 8, kWarps>, p, sm, s); break;

@@ -63,6 +63,9 @@ enum Variant : int32_t {
   V_SX32_F8V1W15T30R12,  // F = 32: 8 frames x 1 voxel, 15 consumer warps, 30 x 4 tiles, 12 slots
   V_SX32_F8V1W15T30R12E, // as V_SX32_F8V1W15T30R12, ring slots released per pair
   V_SX64_C64PE,      // as V_SX64_C64P, ring slots released per pair
+  V_SX16_F4V2W7,     // F = 16 exactly: 4 frames x 2 voxels per lane, 7 consumer warps
+  V_SX16_F4V1W7,     // F = 16 exactly: 4 frames x 1 voxel per lane, 7 consumer warps
+  V_SX8_F4V1W7,      // F = 8 exactly: 4 frames x 1 voxel per lane, 7 consumer warps
   V_COUNT
 };
 

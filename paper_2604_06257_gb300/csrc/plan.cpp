@@ -130,6 +130,8 @@ Variant pick_variant(int iq_dtype, int F) {
     return V_S32_C64;
   }
   if (iq_dtype == MACH_IQ_C64_SPLIT) {   // F % 4 == 0 and F > 4 (checked by validate)
+    if (F == 8) return V_SX8_F4V1W7;
+    if (F == 16) return V_SX16_F4V2W7;
     if (F == 32) return V_SX32_F8V1W7T14E;
     if (F == 64) return V_SX64_C64P;
     if (F <= 16) return V_F32_C64P;
@@ -173,6 +175,7 @@ Variant unstaged(Variant v) {
       return V_F32_C64P;
     case V_ST64_C64P_V4: case V_SX64_C64P: case V_SX64_F8V2: case V_SX64_C64PS: case V_SX64_C64PE:
       return V_F64_C64P;
+    case V_SX16_F4V2W7: case V_SX16_F4V1W7: case V_SX8_F4V1W7: return V_F32_C64P;
     case V_ST64_B16_V4: return V_F64_B16;
     default: return v;
   }
@@ -212,6 +215,7 @@ Variant generic_staged(Variant v) {
     case V_SX32_F8V1W7T14E: case V_SX32_F4V2W7T14: case V_SX32_F8V1W15T30R12: case V_SX32_F8V1W15T30R12E:
       return V_ST32_C64P_V4W7;
     case V_SX64_C64P: case V_SX64_F8V2: case V_SX64_C64PS: case V_SX64_C64PE: return V_ST64_C64P_V4;
+    case V_SX16_F4V2W7: case V_SX16_F4V1W7: case V_SX8_F4V1W7: return V_F32_C64P;
     default: return v;
   }
 }
@@ -487,9 +491,6 @@ mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) 
   if ((st = dev_alloc(reinterpret_cast<void**>(&p->d_elem), sizeof(float4) * C, &p->device_bytes)) != MACH_OK) return fail(st);
   if ((st = dev_alloc(reinterpret_cast<void**>(&p->d_tx), sizeof(float) * T * V, &p->device_bytes)) != MACH_OK) return fail(st);
   if ((st = dev_alloc(reinterpret_cast<void**>(&p->d_err), sizeof(int), &p->device_bytes)) != MACH_OK) return fail(st);
-  if (b.frame_tiles > 1 &&
-      (st = dev_alloc(reinterpret_cast<void**>(&p->d_pd_part), sizeof(float) * b.frame_tiles * V, &p->device_bytes)) != MACH_OK)
-    return fail(st);
   if (list && (st = dev_alloc(reinterpret_cast<void**>(&d_raw), sizeof(float) * 3 * V, &scratch_bytes)) != MACH_OK)
     return fail(st);
   if (!u.empty() && (st = dev_alloc(reinterpret_cast<void**>(&d_u), sizeof(double) * u.size(), &scratch_bytes)) != MACH_OK)
@@ -605,6 +606,12 @@ mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) 
       if ((st = configure_tiles(b, var, list, V, F)) != MACH_OK) return fail(st);
     }
   }
+  // partial Power Doppler sums when the frames span several frame tiles (known once the
+  // variant is final)
+  if (b.frame_tiles > 1 &&
+      (st = dev_alloc(reinterpret_cast<void**>(&p->d_pd_part), sizeof(float) * b.frame_tiles * V, &p->device_bytes)) != MACH_OK)
+    return fail(st);
+  b.pd_part = p->d_pd_part;
   if (d->term_table) {
     // every term evaluated once here; runs read them instead of computing them
     if (!variant_shape(var).staged || !table_supported(var)) return fail(MACH_ERR_UNSUPPORTED);

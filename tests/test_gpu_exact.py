@@ -217,3 +217,42 @@ def test_every_exact_shape_against_the_generic_kernel(name, F):
     else:
         assert nrmse_db(pd_x.cpu().numpy().astype(np.float64), pd_g.cpu().numpy().astype(np.float64)) < -120
     print(name, info["tile"], info["ctas"], check_oracle(acq, iq, y_x, pd_x))
+
+
+def small_2d(F, T=1, seed=0):
+    """A small 2D acquisition (ragged tiles) with F frames and T plane waves, random IQ."""
+    ang = np.linspace(-0.1, 0.1, T) if T > 1 else np.zeros(1)
+    acq = synth.doppler2d(nx=45, nz=29, n_frames=F, n_elem=40, n_samples=600).replace(
+        grid_origin=(-2.2e-3, 0.0, 5e-3), tx_angles=np.stack([ang, np.zeros(T)], 1))
+    return acq, synth.random_iq(acq, 50 + F + seed)
+
+
+@pytest.mark.parametrize("F,T,expect", [(8, 1, "staged_c64p_x8_f4v1w7"), (16, 1, "staged_c64p_x16_f4v2w7"),
+                                        (16, 3, "staged_c64p_x16_f4v2w7"), (8, 5, "staged_c64p_x8_f4v1w7")])
+def test_few_frames(F, T, expect):
+    """8 and 16 frames (exact-frame kernels for short ensembles): the default plan's kernel
+    against the L1-path kernel (same per-frame FMA sequence and, with 32 voxels per warp,
+    the same term order: bitwise frames) and against the oracle."""
+    acq, iq = small_2d(F, T)
+    a = acq.replace(iq_dtype="c64split")
+    kw = m.plan_kwargs(a)
+    x = synth.iqmod.to_c64split(iq.cuda())
+    with m.Plan(**kw) as p:
+        info = p.info()
+        assert info["variant"] == expect
+        pd, y = p.power_doppler(x, want_y=True)
+        y_only = p.run(x)
+        torch.cuda.synchronize()
+        assert p.device_status() == m.MACH_OK
+    assert torch.equal(y, y_only)
+    l1 = "frames_c64p_ft32" if F <= 32 else "frames_c64p_ft64"
+    with forced(kw, l1) as pl:
+        pd_l, y_l = pl.power_doppler(x, want_y=True)
+        torch.cuda.synchronize()
+        same_order = T == 1 or pl.info()["voxels_per_cta"] // 8 == 32
+    if same_order:
+        assert torch.equal(y, y_l)
+    else:
+        assert nrmse_db(y.cpu().numpy(), y_l.cpu().numpy()) < -120
+    assert nrmse_db(pd.cpu().numpy().astype(np.float64), pd_l.cpu().numpy().astype(np.float64)) < -120
+    print(F, T, info["tile"], info["frame_tiles"], check_oracle(acq, iq, y, pd))
