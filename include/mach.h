@@ -244,9 +244,15 @@ mach_status mach_das_terms(mach_plan p, const int64_t *vox_idx_dev, int64_t n,
 /* Lane mapping and voxel tile of one batch instance (chosen by an autotuner, or by
  * mach_batch_plan when not given).  mode 0: frame lanes, `frame_lanes` (4, 8 or 16)
  * lanes share a voxel and each holds 4 frames, so 4 * frame_lanes >= n_frames; one
- * block covers 8 * 4 * (32 / frame_lanes) voxels.  mode 1: channel lanes (n_frames <= 4),
- * 32 voxels per block.  tile: the block's voxel box (x, y, z); its volume must equal the
- * block's voxel count (tile[1] = 1 in 2D), or all zero for the default box. */
+ * block covers 8 * 4 * (32 / frame_lanes) voxels; taps read through L1.  mode 1: channel
+ * lanes (n_frames <= 4), 32 voxels per block.  mode 2: staged windows (the default for
+ * n_frames > 16 that are not a multiple of 4; mode 0 for the other n_frames > 4):
+ * `frame_lanes` 8 (n_frames <= 32) or 16 (n_frames <= 64), 4 frames per lane,
+ * 7 * 4 * (32 / frame_lanes) voxels per block (a producer warp and 7 consumer warps); each usable (element, transmit) pair's sample
+ * window is copied into a shared-memory ring and every term read from there (an instance
+ * whose windows exceed the ring slot takes mode 0 when the shape was not given, else
+ * mach_batch_plan returns UNSUPPORTED).  tile: the block's voxel box (x, y, z); its volume
+ * must equal the block's voxel count (tile[1] = 1 in 2D), or all zero for the default box. */
 typedef struct {
     int32_t mode;
     int32_t frame_lanes;

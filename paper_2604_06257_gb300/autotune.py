@@ -12,7 +12,7 @@ from __future__ import annotations
 import statistics
 from typing import Dict, List, Optional, Tuple
 
-from . import Batch
+from . import Batch, MachError
 
 Shape = Tuple[int, int, Tuple[int, int, int]]
 _CACHE: Dict[tuple, Shape] = {}
@@ -39,11 +39,25 @@ def _boxes(n: int, ndim: int) -> List[Tuple[int, int, int]]:
     return out
 
 
+def _staged_boxes(n: int, ndim: int) -> List[Tuple[int, int, int]]:
+    """Voxel boxes of a staged block (n = 7 x 16 or 7 x 8 voxels): shallow and wide first
+    (a window spans ~2 sample rows per voxel of depth, a fraction of a row per voxel of width)."""
+    if ndim == 2:
+        return [(n // z, 1, z) for z in (2, 4, 7) if n % z == 0]
+    return [(x, y, n // (x * y)) for x, y in ((4, 4), (4, 2), (8, 2), (2, 2)) if n % (x * y) == 0 and n // (x * y) >= 1]
+
+
 def candidates(kw: dict) -> List[Shape]:
+    """Lane mappings and voxel boxes an instance can take: staged windows (mode 2, 8 or 16
+    frame lanes), frame lanes through L1 (mode 0) and, for F <= 4, channel lanes (mode 1)."""
     F = kw["n_frames"]
     cands: List[Shape] = []
     if F <= 4:
         cands += [(1, 0, b) for b in _boxes(32, kw["ndim"])]
+    for fl in (8, 16):
+        if 4 * fl >= F:
+            n = 7 * 4 * (32 // fl)
+            cands += [(2, fl, b) for b in _staged_boxes(n, kw["ndim"])]
     for fl in (4, 8, 16):
         if 4 * fl >= F:
             n = 8 * 4 * (32 // fl)
@@ -86,7 +100,12 @@ def tune_instance(kw: dict, iq, y, pd, max_candidates: Optional[int] = None,
         cands = cands[:max_candidates]
     small = _slab(kw, slab)          # y / pd are large enough for the slab (its voxels come first)
     cands = [c for c in cands]
-    times = {c: time_shape(small, c, iq, y, pd) for c in cands}
+    times = {}
+    for c in cands:
+        try:
+            times[c] = time_shape(small, c, iq, y, pd)
+        except MachError:          # e.g. staged windows that do not fit the ring slot
+            continue
     best = min(times, key=times.get)
     _CACHE[sig] = best
     return best, times

@@ -171,14 +171,16 @@ size_t das_smem_bytes(Variant v);
 // Ragged batches (k_batch.cu / batch.cpp).
 constexpr int kBatchFrames = 0;     // frame lanes (frame_lanes = 4, 8 or 16 lanes per voxel)
 constexpr int kBatchChannels = 1;   // channel lanes (F <= 4)
-struct BatchInstance {
+constexpr int kBatchStaged = 2;     // staged windows (frame_lanes = 8: F <= 32, 16: F <= 64)
+struct alignas(16) BatchInstance {
   DasParams p;          // the instance's tables, tiling and bound buffers
-  int mode;             // kBatchFrames or kBatchChannels
+  int mode;             // kBatchFrames, kBatchChannels or kBatchStaged
   int frame_lanes;
 };
-int batch_blocks_per_sm(int iq_dtype);
+int batch_blocks_per_sm(int iq_dtype, size_t slot_bytes);
+size_t batch_smem_bytes(size_t slot_bytes);
 cudaError_t launch_batch(int iq_dtype, const BatchInstance* insts, const int2* items, int n_items, int* counter,
-                         int grid, cudaStream_t s);
+                         int grid, size_t slot_bytes, cudaStream_t s);
 const DasParams* plan_params(mach_plan p);
 int plan_iq_dtype(mach_plan p);
 void pick_tile_shape(int n, int nx, int ny, int nz, bool list, int tile[3]);

@@ -43,7 +43,10 @@ def test_ragged_batch_matches_oracle(dtype):
         info = b.info()
     assert info["instances"] == 10 and info["items"] >= 10
     modes = [s[0] for s in info["shapes"]]
-    assert modes[:3] == [1, 1, 1] and all(x == 0 for x in modes[3:])
+    # channel lanes for F <= 4; staged windows for F > 16 off the 16-byte grid (frame lanes
+    # where a window exceeds the ring); frame lanes otherwise
+    assert modes[:3] == [1, 1, 1] and all(x in (0, 2) for x in modes[3:]) and 2 in modes
+    assert all(mo == 0 for a, mo in zip(acqs, modes) if 4 < a.n_frames and (a.n_frames <= 16 or a.n_frames % 4 == 0))
     for a, x, y, pd in zip(acqs, stored, ys, pds):
         idx = np.arange(0, a.n_vox, max(1, a.n_vox // 300))
         y_ref, pd_ref = oracle.das(a, synth.iqmod.from_storage(x.cpu()), idx)
@@ -93,6 +96,19 @@ def test_explicit_shapes_and_validation():
         idx = np.arange(0, a.n_vox, max(1, a.n_vox // 200))
         y_ref, _ = oracle.das(a, iq.cpu(), idx)
         assert nrmse_db(y.cpu().numpy()[idx], y_ref) <= -100
+    # staged windows with explicit frame lanes and boxes
+    st = [(1, 0, None), (2, 8, (28, 1, 4) if acqs[1].ndim == 2 else (4, 4, 7)),
+          (2, 16, (14, 1, 4) if acqs[2].ndim == 2 else (4, 2, 7))]
+    with m.Batch(kws, shapes=st) as b:
+        b.bind(iqs, ys, pds)
+        b.run()
+        torch.cuda.synchronize()
+        got = b.info()["shapes"]
+    assert [g[:2] for g in got] == [(1, 0), (2, 8), (2, 16)]
+    for a, iq, y in zip(acqs, iqs, ys):
+        idx = np.arange(0, a.n_vox, max(1, a.n_vox // 200))
+        y_ref, _ = oracle.das(a, iq.cpu(), idx)
+        assert nrmse_db(y.cpu().numpy()[idx], y_ref) <= -100
     bad = [[(1, 0, None), (0, 8, None), (0, 4, None)],          # 4 lanes x 4 frames < 40 frames
            [(0, 8, None), (0, 8, None), (0, 16, None)],         # channel lanes required for F <= 4? no: allowed
            [(1, 0, None), (0, 8, (3, 1, 3)), (0, 16, None)]]    # tile volume mismatch
@@ -100,6 +116,8 @@ def test_explicit_shapes_and_validation():
         m.Batch(kws, shapes=bad[0])
     with pytest.raises(m.MachError):
         m.Batch(kws, shapes=bad[2])
+    with pytest.raises(m.MachError):                          # 8 staged frame lanes hold 32 frames
+        m.Batch(kws, shapes=[(1, 0, None), (0, 8, None), (2, 8, None)])
 
 
 def test_autotuner_picks_a_valid_and_fastest_candidate():
