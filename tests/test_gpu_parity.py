@@ -451,8 +451,9 @@ def test_bounded_wait_reports_timeout_and_context_survives():
 
 @pytest.mark.parametrize("dtype", ["c64", "f16x2", "bf16x2", "c64split"])
 @pytest.mark.parametrize("order", ["ftcs", "tcsf"])
-def test_iq_convert_bit_exact(order, dtype):
-    T, Cn, S, F = 3, 17, 129, 37
+@pytest.mark.parametrize("shape", [(3, 17, 129, 37), (2, 17, 130, 70)])   # odd / even T*C*S (two transposes)
+def test_iq_convert_bit_exact(order, dtype, shape):
+    T, Cn, S, F = shape
     g = torch.Generator(device="cuda").manual_seed(5)
     src_tcsf = torch.view_as_complex(torch.randn((T, Cn, S, F, 2), generator=g, device="cuda") * 3)
     src = src_tcsf.permute(3, 0, 1, 2).contiguous() if order == "ftcs" else src_tcsf.contiguous()
