@@ -439,6 +439,9 @@ def run_ours(args):
     pkg_build.build()
     m.lib()
 
+    frames = synth.make_acquisition(args.workload, "full").n_frames
+    if args.iq_dtype == "c64split" and (frames % 4 or frames <= 4):
+        args.iq_dtype = "c64"          # split rows need a frame count that is a multiple of 4 above 4
     acq, iq = synth.make(args.workload, "full", device=dev, seed=synth.SEEDS[args.workload] + rank,
                          iq_dtype=args.iq_dtype)
     iq_c64 = iq                                     # complex64 [T, C, S, F]
