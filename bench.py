@@ -660,6 +660,10 @@ def run_ours(args):
             torch.cuda.empty_cache()
         extra["ragged"] = ragged_leg(args, flush)
         torch.cuda.empty_cache()
+        # learned compounding (3-angle DAS + U-Net against plain 21-angle DAS, 64 scenes at 128^3)
+        la = argparse.Namespace(**{**vars(args), "steps": 3, "warmup": 3, "no_cpu_baseline": True})
+        extra["learned3d"] = run_learned(la, print_line=False)
+        torch.cuda.empty_cache()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -769,7 +773,7 @@ def run_ragged(args):
 
 # ------------------------------------------------------- learned compounding ----
 
-def run_learned(args):
+def run_learned(args, print_line=True):
     """Learned compounding at 128^3 (matrix array, 1024 elements, 64 scenes per batch on the
     frame axis, split complex64 IQ rows for both paths): 3-angle DAS followed by the
     trained U-Net, against plain 21-angle DAS of the same scenes.  Value = volumes/s of
@@ -791,7 +795,7 @@ def run_learned(args):
     m.lib()
     n, B, nblk = 128, 64, 64
     V = n ** 3
-    params, gain, levels, base = Lc.load(os.path.join(Lc.WEIGHTS_DIR, "unet_few3_many21_128.npz"))
+    params, gain, levels, base, coords = Lc.load(os.path.join(Lc.WEIGHTS_DIR, "unet_few3_many21_128.npz"))
     # held-out scenes: blocks never used in training, complex-weighted, one scene per frame
     acq_blk = Lc.acquisition(n, nblk, "many")
     seeds = range(Lc.TEST_SEED0 + 5000, Lc.TEST_SEED0 + 5000 + nblk)
@@ -808,7 +812,7 @@ def run_learned(args):
     acq_many = Lc.acquisition(n, B, "many").replace(iq_dtype="c64split")
     acq_few = Lc.acquisition(n, B, "few").replace(iq_dtype="c64split")
     pm, pf = m.Plan(**m.plan_kwargs(acq_many)), m.Plan(**m.plan_kwargs(acq_few))
-    net = UNet(n, n, n, B, levels=levels, base_ch=base, inference_only=True)
+    net = UNet(n, n, n, B, levels=levels, base_ch=base, inference_only=True, coords=coords)
     net.set_params(params)
     net.set_gain(gain)
     y_many = torch.empty((V, B), dtype=torch.complex64, device="cuda")
@@ -952,10 +956,12 @@ def run_learned(args):
                     "h2d_bytes_per_step": iq_pin.numel() * iq_pin.element_size(),
                     "d2h_bytes_per_step": out_pin.numel() * out_pin.element_size(), "steps": steps},
             "gpu_launches": (1 + unet_launches) * steps, "clocks": clk}
-    print(json.dumps(line))
     net.close()
     pm.close()
     pf.close()
+    if print_line:
+        print(json.dumps(line))
+    return line
 
 
 # ------------------------------------------------------------ scaling sweep ----

@@ -132,6 +132,11 @@ typedef struct {
     int32_t inference_only; /* non-zero: no gradient, optimiser or data-gradient buffers
                                (about half the memory); backward / train_step then return
                                MACH_ERR_UNSUPPORTED */
+    int32_t coords;     /* non-zero: input channels 2, 3, 4 carry the voxel's position,
+                           c = (2 i + 1 - n) / P per axis (i the index, n the dimension, P
+                           the smallest power of two >= n), so that the network can depend
+                           on where a voxel lies (the point-spread function of a finite
+                           aperture varies across the volume); zero: channels 2.. are 0 */
 } mach_unet_desc;
 
 typedef struct {
@@ -139,7 +144,7 @@ typedef struct {
     int64_t flops_forward;   /* multiply-adds x 2 of one forward pass of one volume */
     int64_t device_bytes;    /* device memory the network holds                     */
     int32_t n_convs;         /* 4L - 1 convolutions                                  */
-    int32_t in_ch;           /* 2: (re, im), padded to base_ch channels             */
+    int32_t in_ch;           /* 2: (re, im), or 5 with coordinates; padded to base_ch */
 } mach_unet_info;
 
 /* Creates the network and its buffers for `batch` volumes of the given size.  Weights

@@ -16,7 +16,8 @@ kernels.  Definitions used here (and by the library):
 * level l has c0 * 2^l channels; encoder a_l = lrelu(conv(in_l)), e_l = lrelu(conv(a_l)),
   in_l = pool(e_{l-1}); decoder (L-2 .. 0) cat_l = [up(d_{l+1}) | e_l] with d_{L-1} = e_{L-1},
   b_l = lrelu(conv(cat_l)), d_l = lrelu(conv(b_l)); output o = conv(d_0);
-* input x = volume / rms (rms over the volume's voxels of |y|), channels (re, im, 0, ...);
+* input x = volume / rms (rms over the volume's voxels of |y|), channels (re, im, 0, ...), or
+  (re, im, cx, cy, cz, 0, ...) with the voxel position as coordinate channels;
   prediction = rms * (gain * x + o[..., :2]); loss = mean over volumes, voxels and
   (re, im) of (o + gain * x - target / rms)^2;
 * Adam (Kingma & Ba 2015, Algorithm 1) with bias correction.
@@ -172,9 +173,19 @@ def unpack(params: np.ndarray, levels: int, base_ch: int):
              params[s.b_off:s.b_off + s.co].astype(np.float64)) for s in layout(levels, base_ch)]
 
 
-def to_channels(y: np.ndarray, dims, base_ch: int) -> Tuple[np.ndarray, np.ndarray]:
+def coord_channel(n: int) -> np.ndarray:
+    """Position of the voxels along an axis of n: (2 i + 1 - n) / P, P the smallest power of
+    two >= n (so |c| < 1, symmetric about the centre)."""
+    P = 1
+    while P < n:
+        P *= 2
+    return (2.0 * np.arange(n) + 1.0 - n) / P
+
+
+def to_channels(y: np.ndarray, dims, base_ch: int, coords: bool = False) -> Tuple[np.ndarray, np.ndarray]:
     """DAS output complex [V, N] -> (x [N, nz, ny, nx, base_ch] with x = y / rms in
-    channels 0, 1; rms [N])."""
+    channels 0, 1 and, with ``coords``, the voxel's x, y, z position in channels 2, 3, 4;
+    rms [N])."""
     nz, ny, nx = dims
     y = np.asarray(y, dtype=np.complex128)
     V, N = y.shape
@@ -184,10 +195,14 @@ def to_channels(y: np.ndarray, dims, base_ch: int) -> Tuple[np.ndarray, np.ndarr
     yn = (y / rms).T.reshape(N, nz, ny, nx)
     x[..., 0] = yn.real
     x[..., 1] = yn.imag
+    if coords:
+        x[..., 2] = coord_channel(nx)[None, None, None, :]
+        x[..., 3] = coord_channel(ny)[None, None, :, None]
+        x[..., 4] = coord_channel(nz)[None, :, None, None]
     return x, rms
 
 
-def forward(params, y_in, dims, levels: int, base_ch: int, gain: float, store=None) -> Dict:
+def forward(params, y_in, dims, levels: int, base_ch: int, gain: float, store=None, coords: bool = False) -> Dict:
     """Forward pass; returns every pre-activation (z_*), activation and the prediction
     (complex [V, N])."""
     q = store if store is not None else (lambda a: a)
@@ -195,7 +210,7 @@ def forward(params, y_in, dims, levels: int, base_ch: int, gain: float, store=No
     L = levels
     enc = lambda l, k: 2 * l + k
     dec = lambda l, k: 2 * L + 2 * (L - 2 - l) + k
-    x, rms = to_channels(y_in, dims, base_ch)
+    x, rms = to_channels(y_in, dims, base_ch, coords)
     A: Dict = {"x": x, "rms": rms, "P": P}
     inp = q(x)
     for l in range(L):
@@ -226,11 +241,12 @@ def forward(params, y_in, dims, levels: int, base_ch: int, gain: float, store=No
     return A
 
 
-def loss_and_grads(params, y_in, target, dims, levels: int, base_ch: int, gain: float, store=None):
+def loss_and_grads(params, y_in, target, dims, levels: int, base_ch: int, gain: float, store=None,
+                   coords: bool = False):
     """(loss, flat gradient, activations) of the loss defined in the module docstring."""
     q = store if store is not None else (lambda a: a)
     L = levels
-    A = forward(params, y_in, dims, levels, base_ch, gain, store)
+    A = forward(params, y_in, dims, levels, base_ch, gain, store, coords)
     P = A["P"]
     spec = layout(levels, base_ch)
     enc = lambda l, k: 2 * l + k
@@ -282,14 +298,14 @@ def loss_and_grads(params, y_in, target, dims, levels: int, base_ch: int, gain: 
     return loss, G, A
 
 
-def he_like(levels: int, base_ch: int, rng: np.random.Generator, scale: float = 1.0) -> np.ndarray:
+def he_like(levels: int, base_ch: int, rng: np.random.Generator, scale: float = 1.0, coords: bool = False) -> np.ndarray:
     """Random parameters (normal, std sqrt(2 / (27 ci)) * scale, biases included) for
     tests; padded input channels are kept at zero like the library's initialisation."""
     p = np.zeros(n_params(levels, base_ch))
     for i, s in enumerate(layout(levels, base_ch)):
         w = rng.standard_normal((27, s.ci, s.co)) * np.sqrt(2.0 / (27 * s.ci)) * scale
         if i == 0:
-            w[:, 2:, :] = 0.0
+            w[:, 5 if coords else 2:, :] = 0.0
         p[s.w_off:s.b_off] = w.ravel()
         p[s.b_off:s.b_off + s.co] = 0.1 * scale * rng.standard_normal(s.co)
     return p

@@ -574,8 +574,16 @@ __device__ __forceinline__ float rms_of(const float* sums, int n, int64_t V) {
   return ms > 0.f ? sqrtf(ms) : 1.f;
 }
 
+// Coordinate channel of index i along an axis of n voxels: (2 i + 1 - n) / P, P the
+// smallest power of two >= n (an integer over a power of two: exact in float).
+__device__ __forceinline__ float coord_of(int64_t i, int n) {
+  int P = 1;
+  while (P < n) P <<= 1;
+  return static_cast<float>(2 * i + 1 - n) / static_cast<float>(P);
+}
+
 __global__ void k_pack(const float2* __restrict__ y, const float* __restrict__ sums, int64_t V, int N, int C,
-                       bf16* __restrict__ xin, float2* __restrict__ xf) {
+                       int coords, int nx, int ny, int nz, bf16* __restrict__ xin, float2* __restrict__ xf) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;   // = n * V + v
   if (i >= V * N) return;
   const int n = static_cast<int>(i / V);
@@ -586,7 +594,15 @@ __global__ void k_pack(const float2* __restrict__ y, const float* __restrict__ s
   xf[i] = x;
   uint4* dst = reinterpret_cast<uint4*>(xin + i * C);
   const __nv_bfloat162 q = __floats2bfloat162_rn(x.x, x.y);
-  dst[0] = make_uint4(*reinterpret_cast<const uint32_t*>(&q), 0u, 0u, 0u);
+  uint4 first = make_uint4(*reinterpret_cast<const uint32_t*>(&q), 0u, 0u, 0u);
+  if (coords) {   // channels 2, 3, 4: the voxel's (x, y, z) position
+    const int64_t ix = v % nx, iy = (v / nx) % ny, iz = v / (static_cast<int64_t>(nx) * ny);
+    const __nv_bfloat162 c01 = __floats2bfloat162_rn(coord_of(ix, nx), coord_of(iy, ny));
+    const __nv_bfloat162 c2 = __floats2bfloat162_rn(coord_of(iz, nz), 0.f);
+    first.y = *reinterpret_cast<const uint32_t*>(&c01);
+    first.z = *reinterpret_cast<const uint32_t*>(&c2);
+  }
+  dst[0] = first;
   for (int k = 1; k < C / 8; ++k) dst[k] = make_uint4(0u, 0u, 0u, 0u);
 }
 
@@ -635,9 +651,10 @@ cudaError_t launch_vol_sumsq(const float2* y, float* sums, float* part, int64_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack(const float2* y, const float* sums, int64_t V, int N, int C, void* xin, float* xf,
-                        cudaStream_t s) {
-  k_pack<<<blocks_for(V * N), 256, 0, s>>>(y, sums, V, N, C, static_cast<bf16*>(xin), reinterpret_cast<float2*>(xf));
+cudaError_t launch_pack(const float2* y, const float* sums, int64_t V, int N, int C, int coords, int nx, int ny,
+                        int nz, void* xin, float* xf, cudaStream_t s) {
+  k_pack<<<blocks_for(V * N), 256, 0, s>>>(y, sums, V, N, C, coords, nx, ny, nz, static_cast<bf16*>(xin),
+                                           reinterpret_cast<float2*>(xf));
   return cudaGetLastError();
 }
 

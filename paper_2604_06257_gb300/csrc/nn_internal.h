@@ -15,7 +15,8 @@ constexpr int kSumBlocks = 608;
 cudaError_t launch_vol_sumsq(const float2* y, float* sums, float* part, int64_t V, int N, cudaStream_t s);
 
 // x = y / rms: xin bf16 [N][V][C] (channels 0, 1 = re, im; the rest 0), xf float [N][V][2]
-cudaError_t launch_pack(const float2* y, const float* sums, int64_t V, int N, int C, void* xin, float* xf,
+cudaError_t launch_pack(const float2* y, const float* sums, int64_t V, int N, int C, int coords, int nx, int ny,
+                        int nz, void* xin, float* xf,
                         cudaStream_t s);
 
 // loss and its gradient for o float [N][V][C] against target complex64 [V][N]

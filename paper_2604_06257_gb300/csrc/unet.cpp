@@ -131,7 +131,8 @@ mach_status conv_bwd(mach_unet_s* u, const Conv& c, void* gout, void* gin, cudaS
 mach_status forward(mach_unet_s* u, const void* x, cudaStream_t s) {
   const int L = u->L, N = u->N;
   TRY(cuda_ok(launch_vol_sumsq(static_cast<const float2*>(x), u->sums, u->sum_part, u->vox1(0), N, s)));
-  TRY(cuda_ok(launch_pack(static_cast<const float2*>(x), u->sums, u->vox1(0), N, u->c0, u->in[0].p, u->xf, s)));
+  TRY(cuda_ok(launch_pack(static_cast<const float2*>(x), u->sums, u->vox1(0), N, u->c0, u->d.coords, u->nx[0],
+                          u->ny[0], u->nz[0], u->in[0].p, u->xf, s)));
   for (int l = 0; l < L; ++l) {
     if (l > 0)
       TRY(mach_nn_pool2(u->e[l - 1].p, u->in[l].p, N, u->nz[l - 1], u->ny[l - 1], u->nx[l - 1], u->ch(l - 1), 0, 0, s));
@@ -260,7 +261,7 @@ mach_status mach_unet_create(const mach_unet_desc* desc, uint64_t seed, mach_une
     c.act = act;
   };
   for (int l = 0; l < L; ++l) {
-    set(u->enc(l, 0), u->in[l].C, l == 0 ? 2 : u->in[l].C, u->ch(l), l, &u->in[l], &u->a[l], true);
+    set(u->enc(l, 0), u->in[l].C, l == 0 ? (d.coords ? 5 : 2) : u->in[l].C, u->ch(l), l, &u->in[l], &u->a[l], true);
     set(u->enc(l, 1), u->ch(l), u->ch(l), u->ch(l), l, &u->a[l], &u->e[l], true);
   }
   for (int l = 0; l < nd; ++l) {
@@ -376,7 +377,7 @@ mach_status mach_unet_get_info(mach_unet net, mach_unet_info* info) {
   info->flops_forward = f;
   info->device_bytes = static_cast<int64_t>(net->arena_bytes);
   info->n_convs = static_cast<int32_t>(net->convs.size());
-  info->in_ch = 2;
+  info->in_ch = net->d.coords ? 5 : 2;
   return MACH_OK;
 }
 

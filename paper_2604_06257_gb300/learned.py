@@ -161,7 +161,7 @@ def evaluate(net, bank: Bank, W: np.ndarray, gain: float) -> Dict[str, float]:
 
 def train(n: int = 128, bank_size: int = 512, samples: int = 2000, epochs: int = 4, batch: int = 8,
           lr: float = 5e-4, seed: int = 0, test_blocks: int = 128, test_scenes: int = 64, levels: int = 4,
-          base_ch: int = 16, warmup: int = 0, log=print):
+          base_ch: int = 16, warmup: int = 0, coords: bool = False, log=print):
     """Train a network from scratch; returns (net, report)."""
     import torch
 
@@ -173,7 +173,7 @@ def train(n: int = 128, bank_size: int = 512, samples: int = 2000, epochs: int =
     torch.cuda.synchronize()
     t_data = time.time() - t0
     gain = ls_gain(bank)
-    net = UNet(n, n, n, batch, levels=levels, base_ch=base_ch, seed=seed)
+    net = UNet(n, n, n, batch, levels=levels, base_ch=base_ch, seed=seed, coords=coords)
     net.set_gain(gain)
     Wtr = scene_weights(rng, bank_size, samples)
     Wte = scene_weights(np.random.default_rng(seed + 7), test_blocks, test_scenes)
@@ -201,7 +201,8 @@ def train(n: int = 128, bank_size: int = 512, samples: int = 2000, epochs: int =
     torch.cuda.synchronize()
     t_train = time.time() - t1
     after = evaluate(net, test, Wte, gain)
-    report = {"n": n, "levels": levels, "base_ch": base_ch, "warmup": warmup, "bank_blocks": bank_size, "train_scenes": samples, "epochs": epochs, "batch": batch,
+    report = {"n": n, "levels": levels, "base_ch": base_ch, "warmup": warmup, "coords": coords,
+              "bank_blocks": bank_size, "train_scenes": samples, "epochs": epochs, "batch": batch,
               "lr": lr, "steps": steps, "gain": gain, "data_s": t_data, "train_s": t_train,
               "ms_per_step": 1e3 * t_train / steps, "test_blocks": test_blocks, "test_scenes": test_scenes,
               "untrained": before, "trained": after, "loss_history": hist}
@@ -213,15 +214,17 @@ def save(net, gain: float, path: str) -> None:
     import torch
     p = torch.as_tensor(net.params()).to(torch.bfloat16).view(torch.int16).numpy()
     d = net.desc
-    np.savez(path, params_bf16=p, gain=np.float64(gain), levels=d.levels, base_ch=d.base_ch)
+    np.savez(path, params_bf16=p, gain=np.float64(gain), levels=d.levels, base_ch=d.base_ch, coords=d.coords)
 
 
 def load(path: str):
-    """(params float32, gain, levels, base_ch) from `save`."""
+    """(params float32, gain, levels, base_ch, coords) from `save` (coords False for files
+    written before the position channels existed)."""
     import torch
     z = np.load(path)
     p = torch.as_tensor(z["params_bf16"]).view(torch.bfloat16).to(torch.float32).numpy()
-    return p, float(z["gain"]), int(z["levels"]), int(z["base_ch"])
+    coords = bool(int(z["coords"])) if "coords" in z.files else False
+    return p, float(z["gain"]), int(z["levels"]), int(z["base_ch"]), coords
 
 
 def main(argv=None):
@@ -236,11 +239,12 @@ def main(argv=None):
     ap.add_argument("--levels", type=int, default=4)
     ap.add_argument("--base-ch", type=int, default=16)
     ap.add_argument("--warmup", type=int, default=0, help="steps of linear learning-rate warm-up")
+    ap.add_argument("--coords", action="store_true", help="voxel position as three extra input channels")
     ap.add_argument("--out", default=os.path.join(WEIGHTS_DIR, "unet_few3_many21_128.npz"))
     ap.add_argument("--report", default=None)
     a = ap.parse_args(argv)
     net, rep = train(a.n, a.bank, a.samples, a.epochs, a.batch, a.lr, a.seed, levels=a.levels, base_ch=a.base_ch,
-                     warmup=a.warmup)
+                     warmup=a.warmup, coords=a.coords)
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
     save(net, rep["gain"], a.out)
     rep["weights"] = os.path.basename(a.out)

@@ -2,23 +2,32 @@
 
 For speckle -- scatterers at uniform random positions with independent N(0, 1)
 amplitudes -- the few-angle (FEW) and many-angle (MANY) DAS volumes are two linear images
-of the same Gaussian scatterer field, hence jointly Gaussian.  The estimator of MANY from
-FEW with the least mean-squared error is then linear, and where the point-spread function
-varies slowly with position it is a Wiener filter in the spatial-frequency domain.  With
-H_F(k), H_M(k) the spectra of the FEW and MANY point-spread functions, a white scatterer
-field and a noise-to-signal ratio lam per frequency, its relative error is
+of the same Gaussian scatterer field, hence jointly Gaussian, and the estimator of MANY
+from FEW with the least mean-squared error is linear.  On the voxel grid the speckle field
+is stationary under whole-voxel shifts, so that estimator is a Wiener filter in the grid's
+frequency domain built from the cross-spectral densities of the two images, averaged over
+where a scatterer sits inside its voxel:
 
-    E(lam) = sum_k |H_M(k)|^2 lam / (|H_F(k)|^2 + lam)  /  sum_k |H_M(k)|^2 ,
+    S_FF(k) = E|F_p(k)|^2,  S_MM(k) = E|M_p(k)|^2,  S_MF(k) = E[M_p(k) F_p(k)*],
 
-and as lam -> 0 it tends to the share of MANY's energy at frequencies FEW does not see.
-No network trained on such scenes can beat E on them; E therefore bounds the learned
-compounding error on speckle (point targets, which are not Gaussian, can do better).
+F_p, M_p the grid spectra of the FEW and MANY images of a unit point at sub-voxel position
+p.  With a noise-to-signal ratio lam per frequency its relative error is
 
-The study beamforms one point scatterer per depth with every transmit of the MANY set
-and of candidate FEW sets separately (mach_das_run_per_tx), on the grid spacing the
-network sees (0.1 mm), and evaluates E for several 3-angle sets:
+    E(lam) = sum_k [S_MM - |S_MF|^2 / (S_FF + lam)] / sum_k S_MM .
 
-    python -m paper_2604_06257_gb300.learned_bound [--depths 8 11 15] [--out report.json]
+If every scatterer sat at the same sub-voxel position, |S_MF|^2 = S_MM S_FF and E would
+vanish as lam -> 0.  It does not: the IQ images carry the axial carrier at twice the
+centre frequency, close to the 0.1 mm grid's Nyquist limit, so the grid samples of a
+point's image depend on where the point sits inside its voxel, and the FEW and MANY
+images decorrelate differently.  No network trained on such scenes can beat E on them;
+E therefore bounds the learned compounding error on speckle (point targets, which are
+not Gaussian, can do better).
+
+The study beamforms a point at K random sub-voxel positions (seeded) with every transmit
+of the MANY set and of candidate FEW sets separately (mach_das_run_per_tx), on the grid
+spacing the network sees (0.1 mm), and evaluates E for several 3-angle sets:
+
+    python -m paper_2604_06257_gb300.learned_bound [--depths 8 11 15] [--positions 48] [--out report.json]
 """
 from __future__ import annotations
 
@@ -44,9 +53,9 @@ CANDIDATES: Dict[str, Tuple[Tuple[float, float], ...]] = {
 LAMBDAS = (1e-2, 1e-3, 1e-4, 1e-6)
 
 
-def point_spectra(z_mm: float, angles_deg: Sequence[Tuple[float, float]], n: int = 64):
-    """|FFT|-domain point-spread spectra: complex128 [T, n, n, n] numpy, one per transmit,
-    of a unit point at (0, 0, z) beamformed on an n^3 grid (0.1 mm) centred on it."""
+def point_spectra(pos_mm, angles_deg: Sequence[Tuple[float, float]], centre_mm, n: int = 64):
+    """Grid spectra complex128 [T, n, n, n] numpy, one per transmit, of a unit point at
+    pos_mm (x, y, z) beamformed on an n^3 grid (0.1 mm) centred on centre_mm."""
     import torch
 
     import synth
@@ -57,9 +66,11 @@ def point_spectra(z_mm: float, angles_deg: Sequence[Tuple[float, float]], n: int
 
     tx = np.deg2rad(np.asarray(angles_deg, dtype=np.float64))
     h = (n - 1) / 2 * 1e-4
+    cx, cy, cz = (c * 1e-3 for c in centre_mm)
     acq = synth.acquisition.volume3d(n=n, n_frames=1, n_samples=1536, tx_angles=tx).replace(
-        grid_origin=(-h, -h, z_mm * 1e-3 - h), name=f"psf_z{z_mm}")
-    iq = simulate_frames(acq, [Phantom(np.array([[0.0, 0.0, z_mm * 1e-3]]), np.array([1.0]))], "cuda")
+        grid_origin=(cx - h, cy - h, cz - h), name="psf")
+    pos = np.asarray(pos_mm, dtype=np.float64)[None, :] * 1e-3
+    iq = simulate_frames(acq, [Phantom(pos, np.array([1.0]))], "cuda")
     T = len(tx)
     with Plan(**plan_kwargs(acq)) as p:
         y = torch.empty((acq.n_vox, T, 1), dtype=torch.complex64, device="cuda")
@@ -68,35 +79,45 @@ def point_spectra(z_mm: float, angles_deg: Sequence[Tuple[float, float]], n: int
     return torch.fft.fftn(vol, dim=(1, 2, 3)).cpu().numpy()
 
 
-def floor_db(HF: np.ndarray, HM: np.ndarray, lams=LAMBDAS) -> Dict[str, float]:
-    """E(lam) in dB for lam relative to max |H_F|^2."""
-    pf, pm = np.abs(HF) ** 2, np.abs(HM) ** 2
+def floor_db(SFF: np.ndarray, SMM: np.ndarray, SMF: np.ndarray, lams=LAMBDAS) -> Dict[str, float]:
+    """E(lam) in dB for lam relative to max S_FF."""
     out = {}
     for lam in lams:
-        L = lam * pf.max()
-        out[f"{lam:g}"] = float(10 * math.log10(np.sum(pm * L / (pf + L)) / np.sum(pm)))
+        L = lam * SFF.max()
+        out[f"{lam:g}"] = float(10 * math.log10(np.sum(SMM - np.abs(SMF) ** 2 / (SFF + L)) / np.sum(SMM)))
     return out
 
 
-def study(depths=(8.0, 11.0, 15.0), n: int = 64) -> dict:
+def study(depths=(8.0, 11.0, 15.0), n: int = 64, positions: int = 48, seed: int = 0) -> dict:
     extra: List[Tuple[float, float]] = []
     for s in CANDIDATES.values():
         for a in s:
             if a not in MANY_DEG and a not in extra:
                 extra.append(a)
     angles = list(MANY_DEG) + extra
-    rep = {"many": [list(a) for a in MANY_DEG], "grid": f"{n}^3 at 0.1 mm centred on the point",
-           "lambda": "noise-to-signal ratio per frequency, relative to max |H_F|^2", "depths_mm": list(depths),
-           "sets": {}}
-    spectra = {z: point_spectra(z, angles, n) for z in depths}
-    for name, s in CANDIDATES.items():
-        idx = [angles.index(a) for a in s]
-        per = {}
-        for z, H in spectra.items():
-            HM = H[: len(MANY_DEG)].sum(0)
-            HF = H[idx].sum(0)
-            per[f"{z:g} mm"] = floor_db(HF, HM)
-        rep["sets"][name] = per
+    nm = len(MANY_DEG)
+    idx = {name: [angles.index(a) for a in s] for name, s in CANDIDATES.items()}
+    rng = np.random.default_rng(seed)
+    rep = {"many": [list(a) for a in MANY_DEG], "grid": f"{n}^3 at 0.1 mm", "positions": positions,
+           "lambda": "noise-to-signal ratio per frequency, relative to max S_FF", "depths_mm": list(depths),
+           "sets": {name: {} for name in CANDIDATES}, "single_position": {name: {} for name in CANDIDATES}}
+    for z in depths:
+        acc = {name: [0.0, 0.0, 0.0] for name in CANDIDATES}
+        for k in range(positions):
+            d = rng.uniform(-0.05, 0.05, 3)   # anywhere inside the voxel around (0, 0, z)
+            H = point_spectra((d[0], d[1], z + d[2]), angles, (0.0, 0.0, z), n)
+            HM = H[:nm].sum(0)
+            for name in CANDIDATES:
+                HF = H[idx[name]].sum(0)
+                a = acc[name]
+                a[0] = a[0] + np.abs(HF) ** 2
+                a[1] = a[1] + np.abs(HM) ** 2
+                a[2] = a[2] + HM * HF.conj()
+                if k == 0:
+                    rep["single_position"][name][f"{z:g} mm"] = floor_db(np.abs(HF) ** 2, np.abs(HM) ** 2,
+                                                                         HM * HF.conj())
+        for name, (sff, smm, smf) in acc.items():
+            rep["sets"][name][f"{z:g} mm"] = floor_db(sff / positions, smm / positions, smf / positions)
     return rep
 
 
@@ -104,11 +125,12 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--depths", type=float, nargs="+", default=[8.0, 11.0, 15.0])
     ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--positions", type=int, default=48)
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     from . import build
     build.build()
-    rep = study(tuple(a.depths), a.n)
+    rep = study(tuple(a.depths), a.n, a.positions)
     for name, per in rep["sets"].items():
         print(name, json.dumps(per))
     if a.out:

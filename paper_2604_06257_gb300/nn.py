@@ -25,7 +25,8 @@ NN_EXPORTS = ("mach_nn_conv3d", "mach_nn_conv3d_tc", "mach_nn_pack_weights", "ma
 
 class mach_unet_desc(C.Structure):
     _fields_ = [("levels", C.c_int32), ("base_ch", C.c_int32), ("batch", C.c_int32),
-                ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("inference_only", C.c_int32)]
+                ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("inference_only", C.c_int32),
+                ("coords", C.c_int32)]
 
 
 class mach_unet_info(C.Structure):
@@ -184,12 +185,13 @@ class UNet:
     """The learned compounding network for `batch` volumes of (nx, ny, nz) voxels.
 
     Volumes in and out are DAS outputs: complex64 [V, batch] CUDA tensors (the batch as
-    the frames axis), V = nx * ny * nz.
+    the frames axis), V = nx * ny * nz.  ``coords``: the voxel's position enters as three
+    extra input channels (mach_unet_desc.coords).
     """
 
     def __init__(self, nx: int, ny: int, nz: int, batch: int, levels: int = 4, base_ch: int = 16,
-                 seed: int = 0, inference_only: bool = False):
-        self.desc = mach_unet_desc(levels, base_ch, batch, nx, ny, nz, int(inference_only))
+                 seed: int = 0, inference_only: bool = False, coords: bool = False):
+        self.desc = mach_unet_desc(levels, base_ch, batch, nx, ny, nz, int(inference_only), int(coords))
         h = C.c_void_p()
         _check(_L().mach_unet_create(C.byref(self.desc), C.c_uint64(seed), C.byref(h)), "mach_unet_create")
         self.handle = h.value

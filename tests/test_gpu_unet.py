@@ -353,6 +353,49 @@ def test_network_forward_backward_matches_oracle(levels, dims, batch, backend):
     assert _rel(G, G64) <= 3e-2 and _cos(G, G64) >= 0.998
 
 
+@pytest.mark.parametrize("dims", [(16, 8, 8), (6, 4, 10)])
+def test_network_with_coordinate_channels_matches_oracle(dims):
+    """Position channels (mach_unet_desc.coords): forward and gradients against the oracle
+    storing the same tensors in bfloat16, including the first layer's weights on the
+    coordinate channels."""
+    nn = _nn()
+    nz, ny, nx = dims
+    V = nz * ny * nx
+    levels, batch, base = 2, 2, 16
+    r = np.random.default_rng(77)
+    p = U.he_like(levels, base, r, coords=True).astype(np.float32)
+    y = (r.standard_normal((V, batch)) + 1j * r.standard_normal((V, batch))).astype(np.complex64)
+    t = (1.5 * y + 0.5 * (r.standard_normal((V, batch)) + 1j * r.standard_normal((V, batch)))).astype(np.complex64)
+    gain = 0.8
+    with nn.UNet(nx, ny, nz, batch, levels=levels, base_ch=base, seed=1, coords=True) as net:
+        net.set_params(p)
+        net.set_gain(gain)
+        yd, td = torch.as_tensor(y).to(dev), torch.as_tensor(t).to(dev)
+        loss = torch.zeros(1, device=dev)
+        net.backward(yd, td, loss)
+        pred = net.forward(yd)
+        torch.cuda.synchronize()
+        G = net.grads()
+    p64 = p.astype(np.float64)
+    lq, Gq, Aq = U.loss_and_grads(p64, y, t, dims, levels, base, gain, store=U.round_bf16, coords=True)
+    assert float(loss.item()) == pytest.approx(lq, rel=2e-3)
+    pr = pred.cpu().numpy().astype(np.complex128)
+    assert _rel(pr - gain * y, Aq["pred"] - gain * y) <= 5e-3
+    assert _rel(G, Gq) <= 5e-3
+    s0 = U.layout(levels, base)[0]
+    w0 = G[s0.w_off:s0.b_off].reshape(27, s0.ci, s0.co)
+    w0q = Gq[s0.w_off:s0.b_off].reshape(27, s0.ci, s0.co)
+    assert np.abs(w0[:, 2:5]).max() > 0
+    assert _rel(w0[:, 2:5], w0q[:, 2:5]) <= 2e-2
+    # without coordinates the same parameters give another prediction
+    with nn.UNet(nx, ny, nz, batch, levels=levels, base_ch=base, seed=1) as net:
+        net.set_params(p)
+        net.set_gain(gain)
+        pred0 = net.forward(yd)
+        torch.cuda.synchronize()
+    assert _rel(pred0.cpu().numpy() - gain * y, pr - gain * y) > 1e-2
+
+
 @pytest.mark.parametrize("backend", ["tcgen05", "mma.sync"])
 def test_five_levels_training_step_keeps_every_weight_copy_current(backend):
     """Five levels: the level-3 decoder convolution reads 256 + 128 channels, so its data

@@ -171,3 +171,40 @@ def test_storage_rounding_is_applied_only_where_stored():
     lq, Gq, A = U.loss_and_grads(p, y, t, dims, levels, base, 1.1, store=U.round_bf16)
     assert 0 < abs(lq - l64) / l64 < 0.05
     assert np.array_equal(A["a0"], U.round_bf16(A["a0"]))   # activations are representable
+
+
+def test_coordinate_channels():
+    """The optional position channels: closed-form values, exact in bfloat16 for grids up
+    to 256, placed in channels 2, 3, 4 (x, y, z) of the packed input, and gradients with
+    respect to first-layer weights on them that match finite differences."""
+    np.testing.assert_array_equal(U.coord_channel(4), [-0.75, -0.25, 0.25, 0.75])
+    np.testing.assert_array_equal(U.coord_channel(5), [-0.5, -0.25, 0.0, 0.25, 0.5])
+    for n in (1, 3, 64, 100, 128, 255, 256):
+        c = U.coord_channel(n)
+        assert np.all(np.abs(c) < 1)
+        np.testing.assert_array_equal(c, -c[::-1])
+        np.testing.assert_array_equal(U.round_bf16(c), c)
+    dims = (3, 4, 5)                                   # (nz, ny, nx), x fastest
+    x, _ = U.to_channels(np.ones((60, 1)), dims, 8, coords=True)
+    assert x[0, 2, 1, 3, 2] == U.coord_channel(5)[3]
+    assert x[0, 2, 1, 3, 3] == U.coord_channel(4)[1]
+    assert x[0, 2, 1, 3, 4] == U.coord_channel(3)[2]
+    assert np.all(x[..., 5:] == 0)
+    levels, base, dims, N = 2, 8, (2, 4, 4), 2
+    r = _rng(9)
+    V = int(np.prod(dims))
+    y = r.standard_normal((V, N)) + 1j * r.standard_normal((V, N))
+    t = 1.5 * y + 0.3 * (r.standard_normal((V, N)) + 1j * r.standard_normal((V, N)))
+    p = U.he_like(levels, base, r, coords=True)
+    gain = 1.1
+    _, G, _ = U.loss_and_grads(p, y, t, dims, levels, base, gain, coords=True)
+    f = lambda q: U.loss_and_grads(q, y, t, dims, levels, base, gain, coords=True)[0]
+    s0 = U.layout(levels, base)[0]
+    h = 1e-6
+    for tap, ci, co in [(13, 2, 0), (4, 3, 5), (22, 4, 7)]:
+        i = s0.w_off + (tap * s0.ci + ci) * s0.co + co
+        e = np.zeros_like(p)
+        e[i] = h
+        fd = (f(p + e) - f(p - e)) / (2 * h)
+        assert G[i] != 0.0
+        assert G[i] == pytest.approx(fd, rel=2e-5, abs=1e-9), (tap, ci, co)
