@@ -89,6 +89,76 @@ __global__ void __launch_bounds__(256) k_transpose_frames2(const float2* __restr
   }
 }
 
+// The 64 x 32 transpose with 16-byte stores as well: a thread writes V consecutive frames of
+// one sample (V = 2 for complex64, 4 for the 16-bit pairs and for split rows), so the frame
+// count must be a multiple of V and the destination 16-byte aligned (split rows: F % 4 == 0
+// puts both rows of every sample on the 16-byte grid).  The tile holds pairs of consecutive
+// samples as 16-byte slots, slot p of frame row f stored at p ^ (f / 2): the row-wise
+// 16-byte stores of the load phase and the column-wise reads of V frames at one sample both
+// spread over all banks.
+template <int DT>
+__global__ void __launch_bounds__(256) k_transpose_frames3(const float2* __restrict__ src, void* __restrict__ dst,
+                                                           int64_t N, int64_t F) {
+  constexpr int NT = 64;
+  constexpr int V = DT == MACH_IQ_C64 ? 2 : 4;
+  constexpr int TPR = 32 / V;            // threads per sample row of 32 frames
+  constexpr int RPP = 256 / TPR;         // sample rows per pass
+  __shared__ float4 tile4[32][NT / 2];
+  const float2(*tile)[NT] = reinterpret_cast<const float2(*)[NT]>(tile4);
+  const int64_t n0 = static_cast<int64_t>(blockIdx.x) * NT;
+  const int64_t f0 = static_cast<int64_t>(blockIdx.y) * 32;
+  float4 v[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int64_t f = f0 + threadIdx.y + 8 * k;
+    const int64_t n = n0 + 2 * threadIdx.x;
+    v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (f < F && n < N) v[k] = __ldg(reinterpret_cast<const float4*>(src + f * N + n));
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int r = threadIdx.y + 8 * k;
+    tile4[r][threadIdx.x ^ (r >> 1)] = v[k];
+  }
+  __syncthreads();
+  // sample j of frame row r, in the swizzled tile
+  auto at = [&](int r, int j) { return tile[r][2 * ((j >> 1) ^ (r >> 1)) + (j & 1)]; };
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const int tc = tid % TPR, tr = tid / TPR;
+  const int fl = V * tc;
+  const int64_t f = f0 + fl;
+  if (f >= F) return;
+#pragma unroll
+  for (int k = 0; k < NT / RPP; ++k) {
+    const int j = tr + k * RPP;
+    const int64_t n = n0 + j;
+    if (n >= N) continue;
+    if constexpr (DT == MACH_IQ_C64) {
+      const float2 a = at(fl, j), b = at(fl + 1, j);
+      *reinterpret_cast<float4*>(static_cast<float2*>(dst) + n * F + f) = make_float4(a.x, a.y, b.x, b.y);
+    } else if constexpr (DT == MACH_IQ_C64_SPLIT) {
+      const float2 a = at(fl, j), b = at(fl + 1, j), c = at(fl + 2, j), d = at(fl + 3, j);
+      float* row = static_cast<float*>(dst) + 2 * n * F;
+      *reinterpret_cast<float4*>(row + f) = make_float4(a.x, b.x, c.x, d.x);
+      *reinterpret_cast<float4*>(row + F + f) = make_float4(a.y, b.y, c.y, d.y);
+    } else {
+      uint32_t h[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float2 a = at(fl + e, j);
+        if constexpr (DT == MACH_IQ_F16X2) {
+          const __half2 q = __float22half2_rn(a);
+          h[e] = *reinterpret_cast<const uint32_t*>(&q);
+        } else {
+          const __nv_bfloat162 q = __float22bfloat162_rn(a);
+          h[e] = *reinterpret_cast<const uint32_t*>(&q);
+        }
+      }
+      *reinterpret_cast<uint4*>(static_cast<uint32_t*>(dst) + n * F + f) = make_uint4(h[0], h[1], h[2], h[3]);
+    }
+  }
+}
+
 // Same layout, storage type only.
 template <int DT>
 __global__ void __launch_bounds__(256) k_cast(const float2* __restrict__ src, void* __restrict__ dst, int64_t total,
@@ -100,7 +170,11 @@ __global__ void __launch_bounds__(256) k_cast(const float2* __restrict__ src, vo
 
 template <int DT>
 cudaError_t convert_as(const float2* src, int order, void* dst, int64_t N, int64_t F, cudaStream_t s) {
-  if (order == 1 && N % 2 == 0 && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+  const bool src16 = (reinterpret_cast<uintptr_t>(src) & 15u) == 0, dst16 = (reinterpret_cast<uintptr_t>(dst) & 15u) == 0;
+  if (order == 1 && N % 2 == 0 && src16 && dst16 && F % (DT == MACH_IQ_C64 ? 2 : 4) == 0) {
+    const dim3 grid(static_cast<unsigned>((N + 63) / 64), static_cast<unsigned>((F + 31) / 32));
+    k_transpose_frames3<DT><<<grid, dim3(32, 8), 0, s>>>(src, dst, N, F);
+  } else if (order == 1 && N % 2 == 0 && src16) {
     const dim3 grid(static_cast<unsigned>((N + 63) / 64), static_cast<unsigned>((F + 31) / 32));
     k_transpose_frames2<DT, 64><<<grid, dim3(32, 8), 0, s>>>(src, dst, N, F);
   } else if (order == 1) {

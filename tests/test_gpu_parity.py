@@ -451,7 +451,9 @@ def test_bounded_wait_reports_timeout_and_context_survives():
 
 @pytest.mark.parametrize("dtype", ["c64", "f16x2", "bf16x2", "c64split"])
 @pytest.mark.parametrize("order", ["ftcs", "tcsf"])
-@pytest.mark.parametrize("shape", [(3, 17, 129, 37), (2, 17, 130, 70)])   # odd / even T*C*S (two transposes)
+# odd T*C*S (8-byte tiles), even T*C*S with F % 4 == 2 (16-byte loads; 16-byte stores for
+# complex64 only) and with F % 4 == 0 (16-byte loads and stores for every storage type)
+@pytest.mark.parametrize("shape", [(3, 17, 129, 37), (2, 17, 130, 70), (2, 5, 66, 36)])
 def test_iq_convert_bit_exact(order, dtype, shape):
     T, Cn, S, F = shape
     g = torch.Generator(device="cuda").manual_seed(5)

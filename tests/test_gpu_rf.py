@@ -37,6 +37,30 @@ def test_rf_to_iq_matches_oracle(shape, taps, decim):
     assert np.all(np.abs(got - ref) <= bound)
 
 
+# Even ensembles of 16 frames or more with up to 16 taps per polyphase branch take the
+# polyphase kernel: several branch counts (P = 1 ... 16), partial frame tiles, a signal
+# shorter than one block's outputs, large decimations (10, 40), many blocks; an odd frame
+# count and a source off the 8-byte grid fall back to the direct kernel.
+@pytest.mark.parametrize("shape,taps,decim,offset", [((2, 3, 301, 32), 17, 2, 0), ((1, 2, 1000, 48), 32, 4, 0),
+                                                     ((1, 1, 50, 16), 33, 4, 0), ((2, 2, 513, 20), 1, 1, 0),
+                                                     ((1, 3, 700, 17), 24, 3, 0), ((1, 1, 4000, 16), 64, 10, 0),
+                                                     ((1, 1, 4000, 16), 64, 40, 0), ((1, 2, 400, 32), 32, 4, 1),
+                                                     ((4, 96, 1200, 32), 32, 4, 0)])
+def test_rf_polyphase_matches_oracle(shape, taps, decim, offset):
+    r = np.random.default_rng(sum(shape) + taps + decim)
+    rf = r.standard_normal(shape).astype(np.float32)
+    h = r.standard_normal(taps).astype(np.float32)
+    fs, fc, t0 = 83.2e6, 5.2e6, 1.3e-6
+    buf = torch.zeros(rf.size + offset, dtype=torch.float32, device="cuda")
+    buf[offset:] = torch.as_tensor(rf.ravel()).cuda()
+    src = buf[offset:].view(shape)
+    got = m.mach_rf_to_iq(src, h, fs, fc, t0, decim).cpu().numpy()
+    ref = rf_oracle.rf_to_iq(rf, h, fs, fc, t0, decim)
+    scale = rf_oracle.rf_to_iq(np.abs(rf), np.abs(h), fs, 0.0, 0.0, decim).real
+    bound = ((taps + 2) * 2.0 ** -24 + 2 * np.pi * shape[2] * 2.0 ** -33 + 1e-6) * scale + 1e-30
+    assert np.all(np.abs(got - ref) <= bound)
+
+
 def test_beamforming_demodulated_rf():
     acq = synth.make_acquisition("bmode2d", "small").replace(n_frames=2)
     ph = phantoms.Phantom(np.array([[0.5e-3, 0.0, 20e-3], [-1.2e-3, 0.0, 17e-3]]), np.array([1.0, 0.6]))
