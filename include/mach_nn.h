@@ -85,6 +85,15 @@ mach_status mach_nn_device_status(void* stream);
  * mach_nn_device_status reports; the context stays usable.  Not thread-safe. */
 void mach_nn_debug_conv(int32_t stall_copies, uint32_t wait_limit);
 
+/* Kernel choice of mach_nn_conv3d_tc (and of the U-Net executor) for 16 output channels with
+ * at most 96 input channels: enable != 0 (the default) uses the x-folded kernel, which
+ * puts the three x taps of each (dz, dy) pair into one N = 48 MMA and shifts the partial
+ * sums by one voxel in its epilogue; enable = 0 the 27-tap kernel.  z_planes: planes per
+ * x-folded tile (1, 2 or 4 (default)); halo_stages: input bricks in flight per CTA (2 ... 4,
+ * 0: as many as keep the CTAs per SM).  Same results up to float32 summation order.  For
+ * tests and measurements; not thread-safe. */
+void mach_nn_set_conv_fold(int32_t enable, int32_t z_planes, int32_t halo_stages);
+
 /* Weight gradient, accumulated:  dw[tap, ci, co] += sum_{n,z,y,x} X[n, z+dz, y+dy, x+dx, ci] *
  * dY[n, z, y, x, co]   (float32 dw, caller zeroes it). */
 mach_status mach_nn_conv3d_wgrad(const void* x, const void* dy, float* dw, int32_t n, int32_t nz, int32_t ny,

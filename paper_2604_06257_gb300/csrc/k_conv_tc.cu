@@ -54,6 +54,9 @@ constexpr uint32_t kResidentMax = 96 * 1024;                 // weights kept who
 __device__ int g_conv_tc_err;   // bit 0: a bounded wait gave up
 uint32_t g_wait_limit = 0;      // test hook: polls per bounded wait (0: default)
 int g_debug_stall = 0;          // test hook: see ConvTcParams::debug_stall, bit 1: the final wait gave up
+int g_conv_fold = 1;            // x-folded kernel for 16 output channels (test hook: 0 = off)
+int g_fold_tz = 4;              // z planes per x-folded tile (1, 2 or 4)
+int g_fold_stages = 0;          // halo stages of the x-folded kernel (0: as many as fit, up to 4)
 
 struct ConvTcParams {
   const bf16* wpk;      // packed weights [Ci/16][27][2][Co][8]
@@ -67,6 +70,7 @@ struct ConvTcParams {
   int tiles_x, tiles_y, tiles_z;
   int64_t tiles;
   uint32_t group_pitch; // bytes between the two 8-channel groups of a halo stage
+  int a_stages;         // halo stages in flight (x-folded kernel: 2 ... 4)
   uint32_t tmem_cols;
   uint32_t wait_limit;
   int debug_stall;      // test hook: the copy warp issues nothing, so every wait runs out
@@ -128,6 +132,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Three tensor-memory loads of 16 columns each, one wait for all of them.
+__device__ __forceinline__ void tmem_ld16x3(uint32_t taddr, uint32_t (&a)[16], uint32_t (&b)[16],
+                                            uint32_t (&c)[16]) {
+#define MACH_TMEM_LD16(dst, addr)                                                                               \
+  asm volatile(                                                                                                \
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];" \
+      : "=r"(dst[0]), "=r"(dst[1]), "=r"(dst[2]), "=r"(dst[3]), "=r"(dst[4]), "=r"(dst[5]), "=r"(dst[6]),       \
+        "=r"(dst[7]), "=r"(dst[8]), "=r"(dst[9]), "=r"(dst[10]), "=r"(dst[11]), "=r"(dst[12]), "=r"(dst[13]),   \
+        "=r"(dst[14]), "=r"(dst[15])                                                                           \
+      : "r"(addr))
+  MACH_TMEM_LD16(a, taddr);
+  MACH_TMEM_LD16(b, taddr + 16);
+  MACH_TMEM_LD16(c, taddr + 32);
+#undef MACH_TMEM_LD16
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 struct TileCoord {
   int n, z0, x0, y0;
 };
@@ -141,6 +162,20 @@ __device__ __forceinline__ TileCoord tile_coord(const ConvTcParams& p, int64_t t
   c.n = static_cast<int>(r / p.tiles_z);
   c.x0 = tx * kTX;
   c.y0 = ty * kTY;
+  return c;
+}
+
+// x-folded tiles: 16 GEMM rows along x starting one voxel before the 14 outputs
+__device__ __forceinline__ TileCoord tile_coord_x(const ConvTcParams& p, int64_t tile) {
+  TileCoord c;
+  const int tx = static_cast<int>(tile % p.tiles_x);
+  int64_t r = tile / p.tiles_x;
+  const int ty = static_cast<int>(r % p.tiles_y);
+  r /= p.tiles_y;
+  c.z0 = static_cast<int>(r % p.tiles_z) * p.tz;
+  c.n = static_cast<int>(r / p.tiles_z);
+  c.x0 = tx * 14 - 1;
+  c.y0 = ty * 8;
   return c;
 }
 
@@ -371,6 +406,227 @@ __global__ void __launch_bounds__(kThreads, 3) k_conv3d_tc(const __grid_constant
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// x-folded variant for 16 output channels.  With N = 16 each MMA reads a 4 KB A operand for
+// 16 columns of work, and the shared-memory operand reads, not the tensor core, set the
+// pace.  Folding the three x taps of a (dz, dy) pair into N gives one N = 48 MMA per pair:
+//   P_j[x'] = sum_ci W[dz, dy, j - 1][ci] X[x' + .., ci]   (j = 0, 1, 2 -> columns 16 j .. 16 j + 15)
+//   Y[x]    = P_0[x - s] + P_1[x] + P_2[x + s]             (s = 1, or -1 with flip)
+// so a tile's GEMM rows are 16 consecutive x positions (no x halo in the A brick) of which
+// the 14 inner ones are outputs; the epilogue shifts the outer column blocks by one row with
+// warp shuffles (rows are x-major, so x +- 1 is lane +- 1).  A tile is 16 (x) x 8 (y) x TZ (z)
+// rows, consecutive tiles 14 apart in x.  The weights are rearranged once per CTA into
+// per-(kc, dz, dy) blocks [g][j * 16 + co][8] (B operand: N = 48 rows 16 bytes apart, the
+// two 8-channel groups 768 bytes apart) and stay resident.
+constexpr int kXR = 16;                 // GEMM rows along x per tile
+constexpr int kXO = kXR - 2;            // outputs along x per tile
+constexpr int kYT = 8;                  // y rows per tile: kXR x kYT = 128
+constexpr int kXN = 48;                 // three x taps x 16 output channels
+constexpr uint32_t kFoldBlock = 2u * kXN * 16u;   // one (dz, dy) pair x 16 input channels
+constexpr int kFoldMaxNC = 6;           // input-channel steps whose weights stay resident
+
+template <bool FLIP, int TZ>
+__global__ void __launch_bounds__(kThreads, 2) k_conv3d_tcx(const __grid_constant__ CUtensorMap xmap,
+                                                            const ConvTcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  const uint32_t a_stage = 2 * p.group_pitch;
+  constexpr uint32_t halo_bytes = static_cast<uint32_t>(kXR * (kYT + 2) * (TZ + 2) * 16);
+  const int NC = p.Ci / 16;
+  const uint32_t w_bytes = static_cast<uint32_t>(NC) * 9u * kFoldBlock;
+  const uint32_t S = static_cast<uint32_t>(p.a_stages);
+  uint8_t* sA = sm;
+  uint8_t* sW = sm + S * a_stage;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sW + w_bytes);
+  uint64_t* fullA = bars;          // [4]
+  uint64_t* emptyA = bars + 4;     // [4]
+  uint64_t* tfull = bars + 8;      // [2]
+  uint64_t* tempty = bars + 10;    // [2]
+  uint64_t* fin = bars + 12;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 13);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // weights: packed [kc][t][g][16][8] -> [kc][dz, dy][g][j * 16 + co][8], t = 3 (dz, dy) + j
+  for (int e = threadIdx.x; e < NC * 9 * 2 * 3 * 16; e += blockDim.x) {
+    const int co = e & 15;
+    int r = e >> 4;
+    const int j = r % 3;
+    r /= 3;
+    const int g = r & 1;
+    r >>= 1;
+    const int pr = r % 9, kc = r / 9;
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p.wpk) + ((kc * 27 + pr * 3 + j) * 2 + g) * 16 + co);
+    *reinterpret_cast<uint4*>(sW + (kc * 9 + pr) * kFoldBlock + (g * kXN + j * 16 + co) * 16) = v;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor core
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 4; ++i) {
+      mbar_init(&fullA[i], 1);
+      mbar_init(&emptyA[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 128);
+    }
+    mbar_init(fin, 1);
+    *abort_flag = 0;
+    mbar_init_fence();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t limit = p.wait_limit;
+
+  auto give_up = [&]() {
+    atomicOr(&g_conv_tc_err, 1);
+    *abort_flag = 1;
+  };
+
+  if (warp == 0) {
+    if (lane == 0 && !p.debug_stall) {   // ----------------------------- copies
+      uint32_t a_use = 0;
+      for (int64_t tile = blockIdx.x; tile < p.tiles && !*abort_flag; tile += gridDim.x) {
+        const TileCoord tc = tile_coord_x(p, tile);
+        for (int kc = 0; kc < NC && !*abort_flag; ++kc) {
+          const uint32_t sa = a_use % S, ka = a_use / S;
+          if (ka >= 1 && !wait_spin(&emptyA[sa], (ka - 1) & 1u, limit)) {
+            give_up();
+            break;
+          }
+          mbar_arrive_expect_tx(&fullA[sa], 2 * halo_bytes);
+          for (int g = 0; g < 2; ++g)
+            tma_load_5d(smem_u32(sA + sa * a_stage + g * p.group_pitch), &xmap, kc * 16 + g * 8, tc.x0, tc.y0 - 1,
+                        tc.z0 - 1, tc.n, &fullA[sa]);
+          ++a_use;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {   // ---------------------------------------------- MMAs
+      constexpr uint32_t idesc = instr_desc(kXN);
+      bool ok = true;
+      uint32_t a_use = 0, acc_use = 0;
+      for (int64_t tile = blockIdx.x; tile < p.tiles && !*abort_flag; tile += gridDim.x) {
+        const uint32_t buf = acc_use & 1u, ku = acc_use >> 1;
+        if (ku >= 1 && !wait_spin(&tempty[buf], (ku - 1) & 1u, limit)) {
+          give_up();
+          break;
+        }
+        fence_after();
+        const uint32_t d0 = tmem + buf * (p.tmem_cols >> 1);
+        for (int kc = 0; kc < NC && ok; ++kc) {
+          const uint32_t sa = a_use % S, ka = a_use / S;
+          if (!wait_spin(&fullA[sa], ka & 1u, limit)) {
+            give_up();
+            ok = false;
+            break;
+          }
+          // A: 8-row groups (x) 128 bytes apart; the (dz, dy) pairs differ by start address
+          const uint64_t ad0 = smem_desc(smem_u32(sA + sa * a_stage), p.group_pitch, 128u);
+          const uint64_t bd0 = smem_desc(smem_u32(sW) + static_cast<uint32_t>(kc) * 9u * kFoldBlock, kXN * 16u, 128u);
+#pragma unroll
+          for (int pr = 0; pr < 9; ++pr) {
+            const int sg = FLIP ? -1 : 1;
+            const int dz = sg * (pr / 3 - 1), dy = sg * (pr % 3 - 1);
+            const uint32_t row = static_cast<uint32_t>((dz + 1) * (kYT + 2) * kXR + (dy + 1) * kXR);
+            const uint64_t bd = bd0 + static_cast<uint64_t>(pr) * (kFoldBlock >> 4);
+            const uint32_t acc = (kc > 0 || pr > 0) ? 1u : 0u;
+#pragma unroll
+            for (int zz = 0; zz < TZ; ++zz)
+              mma_f16(d0 + static_cast<uint32_t>(zz * kXN), ad0 + row + static_cast<uint32_t>(zz * (kYT + 2) * kXR),
+                      bd, idesc, acc);
+          }
+          mma_commit(&emptyA[sa]);
+          ++a_use;
+        }
+        if (!ok) break;
+        mma_commit(&tfull[buf]);
+        ++acc_use;
+      }
+      mma_commit(fin);
+    }
+  } else {   // ---------------------------------------------------------- epilogue
+    const int q = warp & 3;            // tensor-memory lanes 32q .. 32q + 31
+    const int row = 32 * q + lane;     // GEMM row within a plane
+    const int mx = row & (kXR - 1), my = row / kXR;
+    float bias[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) bias[i] = p.bias ? __ldg(&p.bias[i]) : 0.f;
+    uint32_t acc_use = 0;
+    for (int64_t tile = blockIdx.x; tile < p.tiles && !*abort_flag; tile += gridDim.x) {
+      const TileCoord tc = tile_coord_x(p, tile);
+      const uint32_t buf = acc_use & 1u, ku = acc_use >> 1;
+      // warp-uniform: the tensor-memory loads and shuffles below are .sync.aligned
+      if (!__all_sync(0xffffffffu, mbar_wait_bounded(&tfull[buf], ku & 1u, limit))) {
+        if (lane == 0) give_up();
+        break;
+      }
+      __syncwarp();
+      fence_after();
+      const int x = tc.x0 + mx, y = tc.y0 + my;
+      for (int zz = 0; zz < TZ; ++zz) {
+        const int z = tc.z0 + zz;
+        const bool inside = mx >= 1 && mx <= kXO && x < p.W && y < p.H && z < p.D;
+        const int64_t v = ((static_cast<int64_t>(tc.n) * p.D + z) * p.H + y) * p.W + x;
+        const uint32_t taddr = tmem + buf * (p.tmem_cols >> 1) + static_cast<uint32_t>(zz * kXN) +
+                               (static_cast<uint32_t>(32 * q) << 16);
+        uint32_t r0[16], r1[16], r2[16];
+        tmem_ld16x3(taddr, r0, r1, r2);
+        float f[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          // column block 0 comes from row x - s, block 2 from row x + s (16-lane segments = one y row)
+          const float a = FLIP ? __shfl_down_sync(0xffffffffu, __uint_as_float(r0[i]), 1, 16)
+                               : __shfl_up_sync(0xffffffffu, __uint_as_float(r0[i]), 1, 16);
+          const float b = FLIP ? __shfl_up_sync(0xffffffffu, __uint_as_float(r2[i]), 1, 16)
+                               : __shfl_down_sync(0xffffffffu, __uint_as_float(r2[i]), 1, 16);
+          float val = (__uint_as_float(r1[i]) + a) + b + bias[i];
+          if (p.act) val = val > 0.f ? val : kLeak * val;
+          f[i] = val;
+        }
+        if (inside) {
+          if (p.y) {
+            uint32_t h[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+              h[i] = *reinterpret_cast<const uint32_t*>(&b2);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(p.y + v * 16);
+            dst[0] = make_uint4(h[0], h[1], h[2], h[3]);
+            dst[1] = make_uint4(h[4], h[5], h[6], h[7]);
+          }
+          if (p.yf) {
+            float4* dst = reinterpret_cast<float4*>(p.yf + v * 16);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) dst[i] = make_float4(f[4 * i], f[4 * i + 1], f[4 * i + 2], f[4 * i + 3]);
+          }
+        }
+      }
+      fence_before();
+      mbar_arrive(&tempty[buf]);
+      ++acc_use;
+    }
+  }
+
+  __syncthreads();
+  if (warp == 0) {
+    if (!mbar_wait_bounded(fin, 0, limit)) atomicOr(&g_conv_tc_err, 2);
+    __syncwarp();
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
+  }
+}
+
 // bfloat16 weights in the tensor-core layout of both directions:
 //   forward  wpk [Ci/16][27][2][Co][8]:  (kc, t, g, co, j) = W[t][16kc + 8g + j][co]
 //   flipped  wpkt[Co/16][27][2][Ci][8]:  (kc, t, g, ci, j) = W[t][ci][16kc + 8g + j]
@@ -413,7 +669,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 struct TcShape {
-  int tz, resident;
+  int tz, resident, a_stages;
   uint32_t group_pitch, w_bytes, tmem_cols;
   size_t smem;
 };
@@ -444,6 +700,29 @@ TcShape tc_shape(int ci, int co) {
   }
   return shape_for(ci, co, co <= 128 ? 2 : 1);
 }
+
+// x-folded kernel (16 output channels): A bricks of 16 x 10 x (tz + 2) voxels, all weights
+// resident as nc x 9 blocks of 1536 bytes, tz planes x 48 columns x two accumulator buffers
+TcShape shape_fold(int ci, int tz) {
+  TcShape t{};
+  t.tz = tz;
+  const uint32_t halo = static_cast<uint32_t>(kXR * (kYT + 2) * (tz + 2) * 16);
+  t.group_pitch = (halo + 127u) & ~127u;
+  t.resident = 1;
+  t.w_bytes = static_cast<uint32_t>(ci / 16) * 9u * kFoldBlock;
+  uint32_t c = 32;
+  while (c < 2u * static_cast<uint32_t>(tz * kXN)) c <<= 1;
+  t.tmem_cols = c;
+  // as many halo stages (up to 4) as keep the CTAs that tensor memory allows on one SM
+  const size_t budget = c >= 512 ? 220 * 1024 : 110 * 1024;
+  for (t.a_stages = 4; t.a_stages > 2; --t.a_stages)
+    if (1024 + 2 * t.a_stages * static_cast<size_t>(t.group_pitch) + t.w_bytes + 8 * 13 + 16 <= budget) break;
+  if (g_fold_stages >= 2 && g_fold_stages < t.a_stages) t.a_stages = g_fold_stages;
+  t.smem = 1024 + 2 * t.a_stages * static_cast<size_t>(t.group_pitch) + t.w_bytes + 8 * 13 + 16;
+  return t;
+}
+
+bool use_fold(int ci, int co) { return g_conv_fold && co == 16 && ci / 16 <= kFoldMaxNC; }
 
 }  // namespace
 
@@ -515,13 +794,16 @@ cudaError_t launch_conv_tc(const void* x, const void* wpk, const float* bias, vo
                               static_cast<cuuint64_t>(d), static_cast<cuuint64_t>(n)};
   const cuuint64_t row = 2ull * ci;
   const cuuint64_t strides[4] = {row, row * w, row * w * h, row * w * h * d};
-  const cuuint32_t box[5] = {8, kHX, kHY, static_cast<cuuint32_t>(tc_shape(ci, co).tz + 2), 1};
+  const bool fold = use_fold(ci, co);
+  const int ftz = g_fold_tz == 1 || g_fold_tz == 2 ? g_fold_tz : 4;
+  const TcShape shp = fold ? shape_fold(ci, ftz) : tc_shape(ci, co);
+  const cuuint32_t box[5] = {8, static_cast<cuuint32_t>(fold ? kXR : kHX), static_cast<cuuint32_t>(fold ? kYT + 2 : kHY),
+                             static_cast<cuuint32_t>(shp.tz + 2), 1};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(x), dims, strides, box, estr,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
-  const TcShape shp = tc_shape(ci, co);
   ConvTcParams p{};
   p.wpk = static_cast<const bf16*>(wpk);
   p.bias = bias;
@@ -537,18 +819,24 @@ cudaError_t launch_conv_tc(const void* x, const void* wpk, const float* bias, vo
   p.act = act;
   p.tz = shp.tz;
   p.resident = shp.resident;
-  p.tiles_x = (w + kTX - 1) / kTX;
-  p.tiles_y = (h + kTY - 1) / kTY;
+  p.tiles_x = fold ? (w + kXO - 1) / kXO : (w + kTX - 1) / kTX;
+  p.tiles_y = fold ? (h + kYT - 1) / kYT : (h + kTY - 1) / kTY;
   p.tiles_z = (d + shp.tz - 1) / shp.tz;
   p.tiles = static_cast<int64_t>(p.tiles_x) * p.tiles_y * p.tiles_z * n;
   p.group_pitch = shp.group_pitch;
+  p.a_stages = fold ? shp.a_stages : 2;
   p.tmem_cols = shp.tmem_cols;
   p.wait_limit = g_wait_limit ? g_wait_limit : kDefaultWait;
   p.debug_stall = g_debug_stall;
   const size_t smem = shp.smem;
-  auto kern = flip ? (shp.tz == 4 ? k_conv3d_tc<true, 4> : shp.tz == 2 ? k_conv3d_tc<true, 2> : k_conv3d_tc<true, 1>)
-                  : (shp.tz == 4 ? k_conv3d_tc<false, 4>
-                                 : shp.tz == 2 ? k_conv3d_tc<false, 2> : k_conv3d_tc<false, 1>);
+  auto kern = fold ? (flip ? (shp.tz == 4 ? k_conv3d_tcx<true, 4> : shp.tz == 2 ? k_conv3d_tcx<true, 2>
+                                                                      : k_conv3d_tcx<true, 1>)
+                            : (shp.tz == 4 ? k_conv3d_tcx<false, 4> : shp.tz == 2 ? k_conv3d_tcx<false, 2>
+                                                                        : k_conv3d_tcx<false, 1>))
+                   : flip ? (shp.tz == 4 ? k_conv3d_tc<true, 4> : shp.tz == 2 ? k_conv3d_tc<true, 2>
+                                                                     : k_conv3d_tc<true, 1>)
+                          : (shp.tz == 4 ? k_conv3d_tc<false, 4>
+                                         : shp.tz == 2 ? k_conv3d_tc<false, 2> : k_conv3d_tc<false, 1>);
   int per_sm = 0, sms = 0;
   const cudaError_t e = kernel_setup(reinterpret_cast<const void*>(kern), smem, p.tmem_cols, &per_sm, &sms);
   if (e != cudaSuccess) return e;
@@ -598,6 +886,12 @@ mach_status mach_nn_conv3d_tc(const void* x, const void* wpk, const float* bias,
 void mach_nn_debug_conv(int32_t stall_copies, uint32_t wait_limit) {
   g_debug_stall = stall_copies ? 1 : 0;
   g_wait_limit = wait_limit;
+}
+
+void mach_nn_set_conv_fold(int32_t enable, int32_t z_planes, int32_t halo_stages) {
+  g_conv_fold = enable ? 1 : 0;
+  g_fold_tz = z_planes == 1 || z_planes == 2 ? z_planes : 4;
+  g_fold_stages = halo_stages >= 2 && halo_stages <= 4 ? halo_stages : 0;
 }
 
 mach_status mach_nn_device_status(void* stream) {

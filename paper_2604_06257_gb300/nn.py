@@ -15,7 +15,7 @@ import numpy as np
 from . import MachError, _dev_ptr, _stream_ptr, lib
 
 NN_EXPORTS = ("mach_nn_conv3d", "mach_nn_conv3d_tc", "mach_nn_pack_weights", "mach_nn_device_status",
-              "mach_nn_debug_conv",
+              "mach_nn_debug_conv", "mach_nn_set_conv_fold",
               "mach_unet_set_backend", "mach_nn_conv3d_wgrad", "mach_nn_bias_grad", "mach_nn_lrelu_bwd",
               "mach_nn_pool2", "mach_nn_up2", "mach_nn_copy_channels", "mach_nn_adam",
               "mach_unet_create", "mach_unet_destroy", "mach_unet_get_info", "mach_unet_get_params",
@@ -72,6 +72,8 @@ def _L():
             fn.restype = C.c_int
         L.mach_nn_debug_conv.argtypes = [i32, C.c_uint32]
         L.mach_nn_debug_conv.restype = None
+        L.mach_nn_set_conv_fold.argtypes = [i32, i32, i32]
+        L.mach_nn_set_conv_fold.restype = None
         _bound = True
     return L
 
@@ -129,6 +131,10 @@ def mach_nn_device_status(stream=None) -> int:
 
 def mach_nn_debug_conv(stall_copies: bool, wait_limit: int = 0) -> None:
     _L().mach_nn_debug_conv(int(stall_copies), int(wait_limit))
+
+
+def mach_nn_set_conv_fold(enable: bool, z_planes: int = 4, halo_stages: int = 0) -> None:
+    _L().mach_nn_set_conv_fold(int(enable), int(z_planes), int(halo_stages))
 
 
 def mach_nn_conv3d_wgrad(x, dy, dw, stream=None):

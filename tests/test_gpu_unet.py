@@ -140,6 +140,48 @@ def test_conv3d_tcgen05_flip_is_the_data_gradient(ci, co, shape):
     assert np.all(np.abs(gx.cpu().double().numpy() - ref) <= bound)
 
 
+FOLD_CASES = [  # 16 output channels: x tiles of 14 with ragged ends, 1 ... 6 input steps, and 7 (27-tap kernel)
+    (16, (1, 5, 9, 29)), (32, (2, 3, 17, 15)), (48, (1, 4, 8, 14)), (96, (1, 3, 5, 30)), (112, (1, 2, 4, 6)),
+]
+
+
+@pytest.mark.parametrize("ci,shape", FOLD_CASES)
+@pytest.mark.parametrize("tz,stages", [(1, 0), (2, 0), (4, 0), (2, 2), (4, 3)])
+@pytest.mark.parametrize("flip", [False, True])
+def test_conv3d_tcgen05_x_folded_matches_oracle(ci, shape, tz, stages, flip):
+    # the x-folded kernel (three x taps in one N = 48 MMA, partial sums shifted in the
+    # epilogue) against the oracle, forward and flipped, and against the 27-tap kernel
+    nn = _nn()
+    r = np.random.default_rng(ci + 10 * tz + int(flip))
+    x, xh = _bf(r.standard_normal(shape + (ci,)))
+    w, wh = _bf(r.standard_normal((27, ci, 16)) * np.sqrt(2.0 / (27 * ci)))
+    b = torch.as_tensor(r.standard_normal(16).astype(np.float32)).to(dev)
+    wt, wth = _bf(r.standard_normal((27, 16, ci)) * 0.1)   # flipped case: a 16 -> ci convolution
+    ys = []
+    try:
+        for fold in (True, False):
+            nn.mach_nn_set_conv_fold(fold, tz, stages)
+            y = torch.empty(shape + (16,), dtype=torch.float32, device=dev)
+            if flip:   # data gradient of the 16 -> ci convolution: input = its output gradient
+                _, wpkt = nn.mach_nn_pack_weights(wt.float(), 16, ci, forward=False)
+                nn.mach_nn_conv3d_tc(x, wpkt, 16, None, None, y, flip=True)
+                ref = U.conv3d_grad_input(xh, wth)
+                bound = (27 * ci + 2) * 2.0 ** -24 * U.conv3d_grad_input(np.abs(xh), np.abs(wth))
+            else:
+                wpk, _ = nn.mach_nn_pack_weights(w.float(), ci, 16, flipped=False)
+                nn.mach_nn_conv3d_tc(x, wpk, 16, b, None, y, act=True)
+                bb = b.cpu().double().numpy()
+                ref = U.lrelu(U.conv3d(xh, wh, bb))
+                bound = (27 * ci + 2) * 2.0 ** -24 * (U.conv3d(np.abs(xh), np.abs(wh)) + np.abs(bb))
+            assert nn.mach_nn_device_status() == 0
+            got = y.cpu().double().numpy()
+            assert np.all(np.abs(got - ref) <= bound), (fold, np.max(np.abs(got - ref) - bound))
+            ys.append(y)
+    finally:
+        nn.mach_nn_set_conv_fold(True, 4)
+    assert float((ys[0] - ys[1]).abs().max()) <= 1e-5 * float(ys[1].abs().max())
+
+
 def test_tcgen05_and_mma_sync_agree():
     # the two convolution kernels sum the same products in different orders
     nn = _nn()
