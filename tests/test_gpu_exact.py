@@ -17,8 +17,10 @@ from metrics import nrmse_db
 
 pytestmark = pytest.mark.gpu
 
-# (default exact-frame variant, the generic variant it specialises), per frame count
+# (default exact-frame variant, the generic variant it specialises), per frame count; 3D
+# grids with 32 frames default to the exact kernel with 3D tiles of 112 voxels
 PAIRS = {32: ("staged_c64p_x32_f8v1w7t14e", "staged_c64p_ft32_v4w7"), 64: ("staged_c64p_x64_v4", "staged_c64p_ft64_v4")}
+PAIRS_3D = {32: ("staged_c64p_x32_v4w7", "staged_c64p_ft32_v4w7"), 64: PAIRS[64]}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -51,7 +53,7 @@ def run_both(acq, iq_c64, **extra):
     a = acq.replace(iq_dtype="c64split")
     kw = {**m.plan_kwargs(a), **extra}
     x = synth.iqmod.to_c64split(iq_c64.cuda())
-    exact, generic = PAIRS[a.n_frames]
+    exact, generic = (PAIRS_3D if a.vox_pos is None and a.grid_dims[1] > 1 else PAIRS)[a.n_frames]
     with m.Plan(**kw) as pd_plan:
         assert pd_plan.info()["variant"] == exact           # the default choice
     out = []
@@ -80,6 +82,15 @@ def test_exact_equals_generic_bitwise_small(name):
     acq, iq = synth.make(name, "small", device="cpu")
     (y_x, pd_x, _), _ = run_both(acq, iq)
     print(name, check_oracle(acq, iq, y_x, pd_x))
+
+
+def test_exact_3d_32_frames_defaults_to_3d_tiles():
+    """3D grid, 32 frames: the default is the exact kernel with 3D tiles of 112 voxels,
+    bitwise equal to the generic kernel and within the oracle bars."""
+    acq = synth.make_acquisition("ulm3d", "small").replace(n_frames=32)
+    iq = synth.random_iq(acq, 33)
+    (y_x, pd_x, _), _ = run_both(acq, iq)
+    print(check_oracle(acq, iq, y_x, pd_x))
 
 
 def test_exact_equals_generic_bitwise_doppler2d_full():
