@@ -242,9 +242,10 @@ mach_status mach_das_terms(mach_plan p, const int64_t *vox_idx_dev, int64_t n,
 /* ---- ragged batches ---------------------------------------------------------- */
 
 /* Lane mapping and voxel tile of one batch instance (chosen by an autotuner, or by
- * mach_batch_plan when not given).  mode 0: frame lanes, `frame_lanes` (4, 8 or 16)
+ * mach_batch_plan when not given).  mode 0: frame lanes, `frame_lanes` (2, 4, 8 or 16)
  * lanes share a voxel and each holds 4 frames, so 4 * frame_lanes >= n_frames; one
- * block covers 8 * 4 * (32 / frame_lanes) voxels; taps read through L1.  mode 1: channel
+ * block covers 8 * 4 * (32 / frame_lanes) voxels (256 with 2 frame lanes, whose lanes
+ * hold 2 voxels each); taps read through L1.  mode 1: channel
  * lanes (n_frames <= 4), 32 voxels per block.  mode 2: staged windows (the default for
  * n_frames > 16 that are not a multiple of 4; mode 0 for the other n_frames > 4):
  * `frame_lanes` 8 (n_frames <= 32) or 16 (n_frames <= 64), 4 frames per lane,

@@ -58,9 +58,9 @@ def candidates(kw: dict) -> List[Shape]:
         if 4 * fl >= F:
             n = 7 * 4 * (32 // fl)
             cands += [(2, fl, b) for b in _staged_boxes(n, kw["ndim"])]
-    for fl in (4, 8, 16):
+    for fl in (2, 4, 8, 16):
         if 4 * fl >= F:
-            n = 8 * 4 * (32 // fl)
+            n = 256 if fl == 2 else 8 * 4 * (32 // fl)
             cands += [(0, fl, b) for b in _boxes(n, kw["ndim"])]
     return cands
 

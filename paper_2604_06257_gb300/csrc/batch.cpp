@@ -49,13 +49,14 @@ constexpr size_t kBatchSlotCap = 11 * 1024;
 int voxels_per_block(const mach_tile_shape& s) {
   if (s.mode == kBatchChannels) return 32;
   if (s.mode == kBatchStaged) return 7 * 4 * (32 / s.frame_lanes);   // 7 consumer warps + a producer warp
-  return 8 * 4 * (32 / s.frame_lanes);
+  if (s.frame_lanes == 2) return 8 * 2 * 16;   // 8 warps x 16 lane pairs x 2 voxels
+  return 8 * 4 * (32 / s.frame_lanes);         // 8 warps x (32 / FL) lane groups x 4 voxels
 }
 
 // Default lane mapping (measured on the 64-instance float16 batch): channel lanes for
 // F <= 4; staged windows for F > 16 when F is not a multiple of 4 (rows off the 16-byte
 // grid: the L1 path then reads one sample per frame from global memory, the staged path
-// from shared memory); frame lanes through L1 otherwise.
+// from shared memory); frame lanes through L1 otherwise, as few lanes per voxel as cover F.
 mach_tile_shape default_shape(int F) {
   mach_tile_shape s{};
   if (F <= 4) {
@@ -66,7 +67,7 @@ mach_tile_shape default_shape(int F) {
     s.frame_lanes = F <= 32 ? 8 : 16;
   } else {
     s.mode = kBatchFrames;
-    s.frame_lanes = F <= 16 ? 4 : (F <= 32 ? 8 : 16);
+    s.frame_lanes = F <= 8 ? 2 : F <= 16 ? 4 : (F <= 32 ? 8 : 16);
   }
   return s;
 }
@@ -75,7 +76,7 @@ mach_tile_shape default_shape(int F) {
 mach_tile_shape frames_shape(int F) {
   mach_tile_shape s{};
   s.mode = kBatchFrames;
-  s.frame_lanes = F <= 16 ? 4 : (F <= 32 ? 8 : 16);
+  s.frame_lanes = F <= 8 ? 2 : F <= 16 ? 4 : (F <= 32 ? 8 : 16);
   return s;
 }
 
@@ -115,7 +116,8 @@ mach_status mach_batch_plan(const mach_das_desc* descs, int32_t n, const mach_ti
         if (s.frame_lanes != 8 && s.frame_lanes != 16) return MACH_ERR_INVALID_ARG;
         if (4 * s.frame_lanes < descs[i].n_frames) return MACH_ERR_INVALID_ARG;
       } else if (s.mode == kBatchFrames) {
-        if (s.frame_lanes != 4 && s.frame_lanes != 8 && s.frame_lanes != 16) return MACH_ERR_INVALID_ARG;
+        if (s.frame_lanes != 2 && s.frame_lanes != 4 && s.frame_lanes != 8 && s.frame_lanes != 16)
+          return MACH_ERR_INVALID_ARG;
         if (4 * s.frame_lanes < descs[i].n_frames) return MACH_ERR_INVALID_ARG;
       } else {
         return MACH_ERR_INVALID_ARG;

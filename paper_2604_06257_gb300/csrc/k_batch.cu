@@ -15,9 +15,9 @@
 //    evaluate each term once and accumulate 4 frames per lane from shared memory (16-byte
 //    vectors when F % 4 == 0, else one sample per frame).  The ring's barriers are
 //    initialised afresh for every item;
-//  - frame lanes (fallback when an instance's windows exceed the ring): FL lanes share a
-//    voxel (FL = 4, 8 or 16 at run time), each lane holds 4 frames of 4 voxels, taps read
-//    through L1;
+//  - frame lanes (F <= 16 or a multiple of 4, and the fallback when an instance's windows
+//    exceed the ring): FL lanes share a voxel (FL = 2, 4, 8 or 16 at run time), each lane
+//    holds 4 frames of 4 voxels (2 voxels for FL = 2), taps read through L1;
 //  - channel lanes (F <= 4): 8 lanes share a voxel and split its elements; partial sums
 //    meet in a shuffle tree.
 #include <cuda_bf16.h>
@@ -34,9 +34,10 @@ constexpr int kBatchConsumers = kBatchWarps - 1;
 constexpr int kBatchTx = 4;      // transmits whose terms are staged per element round (frame lanes)
 constexpr int kBatchRing = 8;    // ring slots of the staged path
 
-template <class IQ, int VEC, int NV>
+// Frame lanes: FL lanes share a voxel, each holds 4 frames of VPG voxels (VPG = 4, or 2 for
+// FL = 2 so that a warp covers 32 voxels, as with FL = 4); a warp covers (32 / FL) VPG voxels.
+template <class IQ, int VEC, int NV, int VPG>
 __device__ __forceinline__ void batch_frames_tile(const DasParams& p, int FL, int64_t tile, float4* terms) {
-  constexpr int VPG = 4;
   constexpr int FPL = VEC * NV;   // 4 frames per lane
   static_assert(FPL == 4, "four frames per lane");
   const int G = 32 / FL;
@@ -493,10 +494,13 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 2)
       __syncthreads();   // the ring is drained before the next item re-initialises it
     } else if (mode == kBatchChannels) {
       batch_channels_tile<IQ>(p, w.y);
+    } else if (fl == 2) {
+      if (p.F % 4 == 0) batch_frames_tile<IQ, 4, 1, 2>(p, fl, w.y, reinterpret_cast<float4*>(scratch));
+      else batch_frames_tile<IQ, 1, 4, 2>(p, fl, w.y, reinterpret_cast<float4*>(scratch));
     } else if (p.F % 4 == 0) {
-      batch_frames_tile<IQ, 4, 1>(p, fl, w.y, reinterpret_cast<float4*>(scratch));
+      batch_frames_tile<IQ, 4, 1, 4>(p, fl, w.y, reinterpret_cast<float4*>(scratch));
     } else {
-      batch_frames_tile<IQ, 1, 4>(p, fl, w.y, reinterpret_cast<float4*>(scratch));
+      batch_frames_tile<IQ, 1, 4, 4>(p, fl, w.y, reinterpret_cast<float4*>(scratch));
     }
   }
   if (threadIdx.x == 0) {

@@ -120,6 +120,31 @@ def test_explicit_shapes_and_validation():
         m.Batch(kws, shapes=[(1, 0, None), (0, 8, None), (2, 8, None)])
 
 
+def test_two_frame_lanes_for_up_to_eight_frames():
+    """5-8 frames: two lanes per voxel (4 frames each, 2 voxels per lane), by default and
+    with explicit boxes, 2D and 3D, vector and scalar frame loads, against the oracle."""
+    acqs = ragged_instances(n=4, seed=12, iq_dtype="f16x2", scale=0.12)
+    acqs = [a.replace(n_frames=F) for a, F in zip(acqs, [8, 6, 5, 8])]
+    kws = [m.plan_kwargs(a) for a in acqs]
+    iqs, ys, pds = buffers(acqs, seed=90)
+    stored = [synth.iqmod.to_storage(x, "f16x2") for x in iqs]
+    boxes = [None, None, (16, 1, 16) if acqs[2].ndim == 2 else (8, 4, 8),
+             (8, 1, 32) if acqs[3].ndim == 2 else (4, 4, 16)]
+    for shapes in (None, [(0, 2, b) for b in boxes]):
+        with m.Batch(kws, shapes=shapes) as b:
+            b.bind(stored, ys, pds)
+            b.run()
+            torch.cuda.synchronize()
+            assert [g[:2] for g in b.info()["shapes"]] == [(0, 2)] * 4
+        for a, x, y, pd in zip(acqs, stored, ys, pds):
+            idx = np.arange(0, a.n_vox, max(1, a.n_vox // 300))
+            y_ref, pd_ref = oracle.das(a, synth.iqmod.from_storage(x.cpu()), idx)
+            assert nrmse_db(y.cpu().numpy()[idx], y_ref) <= -100, a.name
+            assert nrmse_db(pd.cpu().numpy()[idx].astype(np.float64), pd_ref) <= -60, a.name
+    with pytest.raises(m.MachError):                          # 2 lanes x 4 frames < 9 frames
+        m.Batch([m.plan_kwargs(acqs[0].replace(n_frames=9))], shapes=[(0, 2, None)])
+
+
 def test_autotuner_picks_a_valid_and_fastest_candidate():
     acqs = ragged_instances(n=2, seed=9, iq_dtype="f16x2", scale=0.2)
     kws = [m.plan_kwargs(a) for a in acqs]
