@@ -210,6 +210,46 @@ def test_frame_counts_c64(F):
     print(F, info["variant"], info["frame_tiles"], compare(acq, iq.cpu(), y, pd))
 
 
+@pytest.mark.parametrize("F,dt", [(512, "c64"), (512, "c64split"), (256, "f16x2")])
+def test_largest_swept_frame_counts(F, dt):
+    """The scaling sweep's longest ensembles (frame-tiled kernels) against the oracle."""
+    acq = small_random(F, C=7, T=1, iq_dtype=dt, grid=(9, 1, 7))
+    iq = synth.random_iq(acq, F + 3, device="cuda")
+    diq = dev_iq(acq, iq)
+    with plan_for(acq) as p:
+        pd, y = p.power_doppler(diq, want_y=True)
+        info = p.info()
+    ref_iq = synth.iqmod.from_storage(diq.cpu()) if dt == "f16x2" else iq.cpu()
+    print(F, dt, info["variant"], info["frame_tiles"], compare(acq, ref_iq, y, pd))
+
+
+def test_largest_swept_channel_count():
+    """8192 channels (the sweep's largest array) on the split-row default kernel, sampled voxels."""
+    acq = small_random(32, C=8192, T=1, S=400, iq_dtype="c64split", grid=(33, 1, 17)).replace(
+        elem_pos=synth.acquisition.linear_array(8192, pitch=0.3e-3 * 128 / 8192))
+    iq = synth.random_iq(acq, 81, device="cuda")
+    with plan_for(acq) as p:
+        pd, y = p.power_doppler(dev_iq(acq, iq), want_y=True)
+        info = p.info()
+    idx = np.arange(0, acq.n_vox, 3)
+    print(info["variant"], compare(acq, iq.cpu(), y, pd, idx=idx))
+
+
+def test_largest_swept_voxel_count():
+    """2510 x 2510 pixels (6.3 M voxels, the sweep's largest grid) in the benchmarked kernel,
+    2048 sampled voxels against the oracle."""
+    n, fov = 2510, 25.6e-3
+    step = fov / n
+    acq = synth.doppler2d().replace(grid_dims=(n, 1, n), grid_origin=(-(n - 1) * step / 2, 0.0, 10e-3),
+                                    grid_step=(step, 0.0, step), iq_dtype="c64split")
+    iq = synth.random_iq(acq, 25, device="cuda")
+    with plan_for(acq) as p:
+        pd, y = p.power_doppler(dev_iq(acq, iq), want_y=True)
+        info = p.info()
+    idx = np.sort(np.random.default_rng(25).choice(acq.n_vox, 2048, replace=False))
+    print(info["variant"], compare(acq, iq.cpu(), y, pd, idx=idx))
+
+
 @pytest.mark.parametrize("F", [1, 4, 6, 8, 12, 32, 36, 64, 68, 132])
 def test_frame_counts_f16(F):
     acq = small_random(F, iq_dtype="f16x2")
