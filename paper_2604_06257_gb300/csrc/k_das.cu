@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(256) k_pd_reduce(const float* __restrict__ par
 namespace {
 constexpr int kWarps = 8;
 //                          name                FPL  lanes vox/warp  FT  warps  ch-lanes
-const VariantShape kShapes[V_COUNT] = {
+const VariantShape kShapes[] = {
     //  name                      FPL lanes vox/warp FT  warps ch-lanes staged ring bytes type
     {"channels_c64_cl8",           1,  8,   4,    4,  kWarps, true,  false, 0, 8, 0},
     {"frames_c64_ft16",            2,  8,  32,   16,  kWarps, false, false, 0, 8, 0},
@@ -269,7 +269,10 @@ const VariantShape kShapes[V_COUNT] = {
     {"staged_c64p_x16_f4v2w7",     4,  4,  16,   16,  7,      false, true,  8, 8, 3, 28, true},
     {"staged_c64p_x16_f4v1w7",     4,  4,   8,   16,  7,      false, true,  8, 8, 3, 14, true},
     {"staged_c64p_x8_f4v1w7",      4,  2,  16,    8,  7,      false, true,  8, 8, 3, 28, true},
+    {"channels_c64_cl16",          1, 16,   2,    4,  kWarps, true,  false, 0, 8, 0},
+    {"channels_c64_cl32",          1, 32,   1,    4,  kWarps, true,  false, 0, 8, 0},
 };
+static_assert(sizeof(kShapes) / sizeof(kShapes[0]) == V_COUNT, "one shape row per variant");
 
 template <class K>
 cudaError_t go(K kernel, const DasParams& p, size_t smem, cudaStream_t s) {
@@ -292,6 +295,8 @@ cudaError_t launch_das(const DasParams& p, Variant v, cudaStream_t s) {
   switch (kShapes[v].staged ? V_COUNT : v) {
     case V_COUNT: e = launch_das_staged(p, v, s); break;
     case V_CH_C64: e = go(k_das_channels<float2, 8, 4, kWarps>, p, sm, s); break;
+    case V_CH_C64_L16: e = go(k_das_channels<float2, 16, 4, kWarps>, p, sm, s); break;
+    case V_CH_C64_L32: e = go(k_das_channels<float2, 32, 4, kWarps>, p, sm, s); break;
     case V_F16_C64: e = go(k_das_frames<float2, 2, 1, 8, 8, kWarps>, p, sm, s); break;
     case V_F32_C64: e = go(k_das_frames<float2, 2, 2, 8, 8, kWarps>, p, sm, s); break;
     case V_F64_C64: e = go(k_das_frames<float2, 2, 2, 16, 8, kWarps>, p, sm, s); break;

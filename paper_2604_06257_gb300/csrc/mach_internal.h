@@ -66,6 +66,8 @@ enum Variant : int32_t {
   V_SX16_F4V2W7,     // F = 16 exactly: 4 frames x 2 voxels per lane, 7 consumer warps
   V_SX16_F4V1W7,     // F = 16 exactly: 4 frames x 1 voxel per lane, 7 consumer warps
   V_SX8_F4V1W7,      // F = 8 exactly: 4 frames x 1 voxel per lane, 7 consumer warps
+  V_CH_C64_L16,      // channel lanes, F <= 4, complex64, 16 lanes per voxel
+  V_CH_C64_L32,      // channel lanes, F <= 4, complex64, 32 lanes per voxel
   V_COUNT
 };
 

@@ -210,6 +210,23 @@ def test_frame_counts_c64(F):
     print(F, info["variant"], info["frame_tiles"], compare(acq, iq.cpu(), y, pd))
 
 
+@pytest.mark.parametrize("name", ["channels_c64_cl8", "channels_c64_cl16", "channels_c64_cl32"])
+@pytest.mark.parametrize("F,C", [(1, 9), (3, 33), (4, 128)])
+def test_channel_lane_widths(name, F, C):
+    """8, 16 or 32 lanes per voxel splitting its elements (shuffle-tree partial sums)."""
+    acq = small_random(F, C=C, T=3)
+    iq = synth.random_iq(acq, 40 + F + C, device="cuda")
+    m.mach_debug_force_variant(name)
+    try:
+        p = plan_for(acq)
+    finally:
+        m.mach_debug_force_variant(None)
+    with p:
+        assert p.info()["variant"] == name
+        pd, y = p.power_doppler(iq, want_y=True)
+    compare(acq, iq.cpu(), y, pd)
+
+
 @pytest.mark.parametrize("F,dt", [(512, "c64"), (512, "c64split"), (256, "f16x2")])
 def test_largest_swept_frame_counts(F, dt):
     """The scaling sweep's longest ensembles (frame-tiled kernels) against the oracle."""
