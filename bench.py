@@ -108,18 +108,23 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(variant: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel sources; else None."""
+def profiled_entry(variant: str, workload: str) -> dict:
+    """The committed ncu figures of one launch (DRAM bytes, L2 bytes and the L2 peak
+    sector rate), if they were taken on the current kernel sources; else {}."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         data = json.load(open(path))
     except (OSError, ValueError):
-        return None
+        return {}
     e = data.get(f"{variant}@{workload}")
     if not e or e.get("kernel_sha") != kernel_hash():
-        return None
-    return e.get("dram_bytes_per_launch")
+        return {}
+    return e
+
+
+def profiled_traffic(variant: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, or None."""
+    return profiled_entry(variant, workload).get("dram_bytes_per_launch")
 
 
 class Clocks:
@@ -523,7 +528,8 @@ def run_ours(args):
     achieved = flops / t_launch / 1e12
     comp = counts.compulsory_bytes(V, acq.n_elem, acq.n_tx, acq.n_samples, F, write_y=True, write_pd=True,
                                    iq_bytes=8 if args.iq_dtype in ("c64", "c64split") else 4)
-    traffic = profiled_traffic(info["variant"] + ("+table" if args.term_table else ""), acq.name)
+    prof = profiled_entry(info["variant"] + ("+table" if args.term_table else ""), acq.name)
+    traffic = prof.get("dram_bytes_per_launch")
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": traffic,
             "kernel": info["variant"],
@@ -540,6 +546,12 @@ def run_ours(args):
                              "peak_source": f"shared-memory load path: {n_sm} SMs x 128 B/clk x {sm_max:.0f} MHz",
                              "frac": active_points * (16 if args.iq_dtype in ("c64", "c64split") else 8)
                              / t_launch / (n_sm * 128 * sm_max * 1e6)}}
+    if prof.get("l2_bytes_per_launch") and prof.get("l2_peak_gbs"):
+        l2 = float(prof["l2_bytes_per_launch"])
+        roof["l2"] = {"bytes_per_launch": l2, "achieved_gbs": l2 / t_launch / 1e9, "peak_gbs": prof["l2_peak_gbs"],
+                      "frac": l2 / t_launch / 1e9 / prof["l2_peak_gbs"],
+                      "source": "ncu lts__t_sectors of one launch (profiles/traffic.json); peak = the "
+                                "counter's peak sector rate x 32 B"}
 
     # K0 (channel-data preparation): acquisition order -> frame-contiguous layout, per
     # storage type; HBM-bound, so it is reported against the measured copy bandwidth
