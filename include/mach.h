@@ -310,12 +310,13 @@ mach_status mach_plan_device_status(mach_plan p, void *stream);
  * call), iq_dev as for mach_das_run, outputs y_dev_or_null (complex64 [n_vox][n_frames])
  * and/or pd_dev_or_null (float32 [n_vox]), at least one of them.
  * Errors: INVALID_ARG as for a plan or a NULL/misaligned buffer; UNSUPPORTED when the
- * tables exceed the 8 MiB array.  The tables are, each rounded up to a multiple of 256 B:
+ * tables exceed the 8 MiB array or when `stream` is being captured into a CUDA graph (the
+ * call copies from host buffers that do not outlive it).  The tables are, each rounded up to a multiple of 256 B:
  * 16 B per voxel; 16 B per element; 4 B per voxel and transmit; 24 B per transmit for
  * plane waves (none with tx_table_dev); 12 B per voxel for a voxel list; 4 B per voxel
  * and frame tile for Power Doppler over more than one frame tile.  CUDA on a failed
  * copy or launch (the runtime's last error is cleared).  Nothing is enqueued on argument
- * errors or when the tables do not fit.
+ * errors, when the tables do not fit or during a capture.
  * The first call on a device looks up the array's device address (do it before any
  * stream capture).  Calls share the array, so calls that overlap on the GPU race;
  * order them on one stream.  Returns after the host arrays are copied; the

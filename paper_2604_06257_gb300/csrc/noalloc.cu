@@ -102,6 +102,11 @@ extern "C" mach_status mach_das_run_noalloc(const mach_das_desc* d, const void* 
   const bool need_part = b.frame_tiles > 1 && pd_dev_or_null;
   const size_t end = off_part + align256(need_part ? sizeof(float) * static_cast<size_t>(b.frame_tiles) * V : 0);
   if (end > kScratchBytes) return MACH_ERR_UNSUPPORTED;
+  // The host arrays below are copied from this call's own (pageable, short-lived) buffers;
+  // a graph captured around the call would read them again at replay, after they are gone.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return cuda_fail();
+  if (cap != cudaStreamCaptureStatusNone) return MACH_ERR_UNSUPPORTED;
 
   unsigned char* base = nullptr;
   if ((st = scratch_address(&base)) != MACH_OK) return st;

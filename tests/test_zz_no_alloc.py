@@ -116,3 +116,18 @@ def test_noalloc_rejects_tables_beyond_the_fixed_array():
     assert st == m.MACH_ERR_UNSUPPORTED
     torch.cuda.synchronize()
     assert torch.count_nonzero(y).item() == 0
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """Inside a CUDA-graph capture the call is refused before it enqueues anything (its
+    host copies would be replayed from buffers that no longer exist)."""
+    acq, iq = synth.make("doppler2d", "small", device="cuda")
+    d, keep = m.make_desc(**m.plan_kwargs(acq))
+    y = torch.zeros((acq.n_vox, acq.n_frames), dtype=torch.complex64, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        st = m.lib().mach_das_run_noalloc(C.byref(d), iq.data_ptr(), y.data_ptr(), None, s.cuda_stream)
+    assert st == m.MACH_ERR_UNSUPPORTED
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(y).item() == 0
