@@ -271,6 +271,8 @@ const VariantShape kShapes[] = {
     {"staged_c64p_x8_f4v1w7",      4,  2,  16,    8,  7,      false, true,  8, 8, 3, 28, true},
     {"channels_c64_cl16",          1, 16,   2,    4,  kWarps, true,  false, 0, 8, 0},
     {"channels_c64_cl32",          1, 32,   1,    4,  kWarps, true,  false, 0, 8, 0},
+    {"staged_c64p_x64_v4t16",      4, 16,   8,   64,  kWarps, false, true,  8, 8, 3, 16, true},
+    {"staged_c64p_x64_v4t16e",     4, 16,   8,   64,  kWarps, false, true,  8, 8, 3, 16, true},
 };
 static_assert(sizeof(kShapes) / sizeof(kShapes[0]) == V_COUNT, "one shape row per variant");
 

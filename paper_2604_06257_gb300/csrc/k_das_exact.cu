@@ -342,7 +342,9 @@ cudaError_t launch_das_exact(const DasParams& p, Variant v, cudaStream_t s) {
     case V_SX32_F4V2W7T14: return go_staged(k_das_exact<32, 4, 2, 7, 8, 64, 0>, 7, p, sm, s);
     case V_SX32_F8V1W15T30R12: return go_staged(k_das_exact<32, 8, 1, 15, 12, 64, 0>, 15, p, sm, s);
     case V_SX32_F8V1W15T30R12E: return go_staged(k_das_exact<32, 8, 1, 15, 12, 64, kEarly>, 15, p, sm, s);
-    case V_SX64_C64P: return go_staged(k_das_exact<64, 4, 4, 8, 8, 72, 0>, 8, p, sm, s);
+    case V_SX64_C64P: case V_SX64_C64P_T16:
+      return go_staged(k_das_exact<64, 4, 4, 8, 8, 72, 0>, 8, p, sm, s);
+    case V_SX64_C64P_T16E: return go_staged(k_das_exact<64, 4, 4, 8, 8, 72, kEarly>, 8, p, sm, s);
     case V_SX64_C64PS: return go_staged(k_das_exact<64, 4, 4, 8, 8, 72, kSleep>, 8, p, sm, s);
     case V_SX64_C64PE: return go_staged(k_das_exact<64, 4, 4, 8, 8, 72, kEarly>, 8, p, sm, s);
     case V_SX64_F8V2: return go_staged(k_das_exact<64, 8, 2, 8, 8, 72, 0>, 8, p, sm, s);

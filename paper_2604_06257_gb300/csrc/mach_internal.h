@@ -68,6 +68,8 @@ enum Variant : int32_t {
   V_SX8_F4V1W7,      // F = 8 exactly: 4 frames x 1 voxel per lane, 7 consumer warps
   V_CH_C64_L16,      // channel lanes, F <= 4, complex64, 16 lanes per voxel
   V_CH_C64_L32,      // channel lanes, F <= 4, complex64, 32 lanes per voxel
+  V_SX64_C64P_T16,   // as V_SX64_C64P with 16 x 4 voxel tiles (2D)
+  V_SX64_C64P_T16E,  // as V_SX64_C64P_T16, ring slots released per pair
   V_COUNT
 };
 

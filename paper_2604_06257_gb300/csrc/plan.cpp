@@ -174,6 +174,7 @@ Variant unstaged(Variant v) {
     case V_SX32_F8V1W15T30R12: case V_SX32_F8V1W15T30R12E:
       return V_F32_C64P;
     case V_ST64_C64P_V4: case V_SX64_C64P: case V_SX64_F8V2: case V_SX64_C64PS: case V_SX64_C64PE:
+    case V_SX64_C64P_T16: case V_SX64_C64P_T16E:
       return V_F64_C64P;
     case V_SX16_F4V2W7: case V_SX16_F4V1W7: case V_SX8_F4V1W7: return V_F32_C64P;
     case V_ST64_B16_V4: return V_F64_B16;
@@ -214,7 +215,9 @@ Variant generic_staged(Variant v) {
     case V_SX32_F8V1W15T24: case V_SX32_F8V1W15T40: case V_SX32_F8V1W15T24S: case V_SX32_F8V1W7T14:
     case V_SX32_F8V1W7T14E: case V_SX32_F4V2W7T14: case V_SX32_F8V1W15T30R12: case V_SX32_F8V1W15T30R12E:
       return V_ST32_C64P_V4W7;
-    case V_SX64_C64P: case V_SX64_F8V2: case V_SX64_C64PS: case V_SX64_C64PE: return V_ST64_C64P_V4;
+    case V_SX64_C64P: case V_SX64_F8V2: case V_SX64_C64PS: case V_SX64_C64PE: case V_SX64_C64P_T16:
+    case V_SX64_C64P_T16E:
+      return V_ST64_C64P_V4;
     case V_SX16_F4V2W7: case V_SX16_F4V1W7: case V_SX8_F4V1W7: return V_F32_C64P;
     default: return v;
   }
@@ -418,6 +421,10 @@ mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) 
   // 3D grids with 32 frames: the exact kernel's 112-voxel 3D tiles (4 frames per lane) beat
   // its shallow 14 x 4 tiles (94 x 94 x 178 voxels, 1024 elements: 2.29 against 2.10 T points/s)
   if (var == V_SX32_F8V1W7T14E && !list && d->grid_dims[1] > 1) var = V_SX32_C64P;
+  // 2D grids with 64 frames: shallow 16 x 4 tiles keep the windows short enough for the
+  // 8-slot ring of 512-byte rows (the squarest 8 x 8 tiles do not fit; the L1 path then
+  // ran 256 x 256 px at 1.47 against 2.11 T points/s)
+  if (var == V_SX64_C64P && !list && d->grid_dims[1] == 1) var = V_SX64_C64P_T16;
   if (d->term_table) var = generic_staged(var);
   const bool forced = g_force_variant >= 0;
   if (forced) {

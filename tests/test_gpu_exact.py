@@ -93,6 +93,27 @@ def test_exact_3d_32_frames_defaults_to_3d_tiles():
     print(check_oracle(acq, iq, y_x, pd_x))
 
 
+def test_exact_2d_64_frames_shallow_tiles():
+    """2D grid, 64 frames: the default takes 16 x 4 voxel tiles (whose windows fit the ring),
+    against the oracle; per-pair slot release changes no bit."""
+    acq = synth.make_acquisition("doppler2d", "small").replace(n_frames=64, iq_dtype="c64split")
+    iq = synth.random_iq(acq, 64)
+    x = synth.iqmod.to_c64split(iq.cuda())
+    kw = m.plan_kwargs(acq)
+    out = []
+    with m.Plan(**kw) as p:
+        info = p.info()
+        assert info["variant"] == "staged_c64p_x64_v4t16" and info["tile"] == [16, 1, 4]
+        out.append(p.power_doppler(x, want_y=True))
+    with forced(kw, "staged_c64p_x64_v4t16e") as p:
+        out.append(p.power_doppler(x, want_y=True))
+        torch.cuda.synchronize()
+        assert p.device_status() == m.MACH_OK
+    (pd0, y0), (pd1, y1) = out
+    assert torch.equal(y0, y1) and torch.equal(pd0, pd1)
+    print(check_oracle(acq, iq, y0, pd0))
+
+
 def test_exact_equals_generic_bitwise_doppler2d_full():
     """The benchmark workload in the benchmarked launch configuration."""
     acq, iq = synth.make("doppler2d", "full", device="cuda")
@@ -195,7 +216,8 @@ SHAPES = [("staged_c64p_x32_v4w7", 32), ("staged_c64p_x32_f4v2w7", 32), ("staged
           ("staged_c64p_x64_f8v2", 64), ("staged_c64p_x32_f8v1w15t24", 32), ("staged_c64p_x32_f8v1w15t40", 32),
           ("staged_c64p_x32_f8v1w15t24s", 32), ("staged_c64p_x64_v4s", 64), ("staged_c64p_x32_f8v1w7t14", 32),
           ("staged_c64p_x32_f8v1w7t14e", 32), ("staged_c64p_x32_f4v2w7t14", 32), ("staged_c64p_x32_f8v1w15t30r12", 32),
-          ("staged_c64p_x32_f8v1w15t30r12e", 32), ("staged_c64p_x64_v4e", 64)]
+          ("staged_c64p_x32_f8v1w15t30r12e", 32), ("staged_c64p_x64_v4e", 64), ("staged_c64p_x64_v4t16", 64),
+          ("staged_c64p_x64_v4t16e", 64)]
 
 
 @pytest.mark.parametrize("name,F", SHAPES)
