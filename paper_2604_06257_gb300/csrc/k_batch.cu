@@ -124,7 +124,8 @@ __device__ __forceinline__ void batch_frames_tile(const DasParams& p, int FL, in
             *reinterpret_cast<float4*>(dst + 2) = make_float4(acc[k][mm * 4 + 2].x, acc[k][mm * 4 + 2].y,
                                                               acc[k][mm * 4 + 3].x, acc[k][mm * 4 + 3].y);
           } else {
-            p.y[v * p.F + f] = acc[k][mm];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) p.y[v * p.F + f + e] = acc[k][mm * VEC + e];
           }
         }
       }
@@ -482,12 +483,15 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 2)
       } else {
         float4* terms = reinterpret_cast<float4*>(scratch);
         float* txc = reinterpret_cast<float*>(scratch + 32 * 16);
-        const bool vec = p.F % 4 == 0;
+        // 16-byte vectors when F % 4 == 0, 8-byte pairs for the other even F, else single samples
+        const int vec = p.F % 4 == 0 ? 4 : (p.F % 2 == 0 ? 2 : 1);
         if (fl == 16) {
-          if (vec) batch_consume<IQ, 4, 1, 16>(p, w.y, warp, lane, smem, slot_bytes, terms, txc, meta, full, empty);
+          if (vec == 4) batch_consume<IQ, 4, 1, 16>(p, w.y, warp, lane, smem, slot_bytes, terms, txc, meta, full, empty);
+          else if (vec == 2) batch_consume<IQ, 2, 2, 16>(p, w.y, warp, lane, smem, slot_bytes, terms, txc, meta, full, empty);
           else batch_consume<IQ, 1, 4, 16>(p, w.y, warp, lane, smem, slot_bytes, terms, txc, meta, full, empty);
         } else {
-          if (vec) batch_consume<IQ, 4, 1, 8>(p, w.y, warp, lane, smem, slot_bytes, terms, txc, meta, full, empty);
+          if (vec == 4) batch_consume<IQ, 4, 1, 8>(p, w.y, warp, lane, smem, slot_bytes, terms, txc, meta, full, empty);
+          else if (vec == 2) batch_consume<IQ, 2, 2, 8>(p, w.y, warp, lane, smem, slot_bytes, terms, txc, meta, full, empty);
           else batch_consume<IQ, 1, 4, 8>(p, w.y, warp, lane, smem, slot_bytes, terms, txc, meta, full, empty);
         }
       }
@@ -496,9 +500,12 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 2)
       batch_channels_tile<IQ>(p, w.y);
     } else if (fl == 2) {
       if (p.F % 4 == 0) batch_frames_tile<IQ, 4, 1, 2>(p, fl, w.y, reinterpret_cast<float4*>(scratch));
+      else if (p.F % 2 == 0) batch_frames_tile<IQ, 2, 2, 2>(p, fl, w.y, reinterpret_cast<float4*>(scratch));
       else batch_frames_tile<IQ, 1, 4, 2>(p, fl, w.y, reinterpret_cast<float4*>(scratch));
     } else if (p.F % 4 == 0) {
       batch_frames_tile<IQ, 4, 1, 4>(p, fl, w.y, reinterpret_cast<float4*>(scratch));
+    } else if (p.F % 2 == 0) {
+      batch_frames_tile<IQ, 2, 2, 4>(p, fl, w.y, reinterpret_cast<float4*>(scratch));
     } else {
       batch_frames_tile<IQ, 1, 4, 4>(p, fl, w.y, reinterpret_cast<float4*>(scratch));
     }

@@ -59,9 +59,13 @@ __device__ __forceinline__ void load_vec(const IQ* p, float2 (&o)[VEC]) {
       }
     }
   } else if constexpr (std::is_same<IQ, __half2>::value) {
-    static_assert(VEC == 1 || VEC == 4, "1 or 4 samples");
+    static_assert(VEC == 1 || VEC == 2 || VEC == 4, "1, 2 or 4 samples");
     if constexpr (VEC == 1) {
       o[0] = __half22float2(ld<SMEM>(p));
+    } else if constexpr (VEC == 2) {
+      const uint2 v = ld<SMEM>(reinterpret_cast<const uint2*>(p));
+      o[0] = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+      o[1] = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
     } else {
       const uint4 v = ld<SMEM>(reinterpret_cast<const uint4*>(p));
       o[0] = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
@@ -70,9 +74,13 @@ __device__ __forceinline__ void load_vec(const IQ* p, float2 (&o)[VEC]) {
       o[3] = __half22float2(*reinterpret_cast<const __half2*>(&v.w));
     }
   } else {
-    static_assert(VEC == 1 || VEC == 4, "1 or 4 samples");
+    static_assert(VEC == 1 || VEC == 2 || VEC == 4, "1, 2 or 4 samples");
     if constexpr (VEC == 1) {
       o[0] = widen_bf16x2(ld<SMEM>(reinterpret_cast<const unsigned int*>(p)));
+    } else if constexpr (VEC == 2) {
+      const uint2 v = ld<SMEM>(reinterpret_cast<const uint2*>(p));
+      o[0] = widen_bf16x2(v.x);
+      o[1] = widen_bf16x2(v.y);
     } else {
       const uint4 v = ld<SMEM>(reinterpret_cast<const uint4*>(p));
       o[0] = widen_bf16x2(v.x);

@@ -32,8 +32,11 @@ def buffers(acqs, seed=0):
 
 @pytest.mark.parametrize("dtype", ["c64", "f16x2"])
 def test_ragged_batch_matches_oracle(dtype):
-    acqs = ragged_instances(n=10, seed=11, iq_dtype=dtype, scale=0.12)
-    acqs = [a.replace(n_frames=F) for a, F in zip(acqs, [1, 3, 4, 5, 7, 12, 17, 33, 48, 64])]
+    # frame counts for every lane mapping and load width: channel lanes (F <= 4), two frame
+    # lanes (5-8), single samples (odd F), 8-byte pairs (even F off the 16-byte grid: 10,
+    # 18, 34), 16-byte vectors (F % 4 == 0), staged windows (F > 16 off the grid)
+    acqs = ragged_instances(n=13, seed=11, iq_dtype=dtype, scale=0.12)
+    acqs = [a.replace(n_frames=F) for a, F in zip(acqs, [1, 3, 4, 5, 7, 10, 12, 17, 18, 33, 34, 48, 64])]
     iqs, ys, pds = buffers(acqs)
     stored = [synth.iqmod.to_storage(x, dtype) for x in iqs]
     with m.Batch([m.plan_kwargs(a) for a in acqs]) as b:
@@ -41,7 +44,7 @@ def test_ragged_batch_matches_oracle(dtype):
         b.run()
         torch.cuda.synchronize()
         info = b.info()
-    assert info["instances"] == 10 and info["items"] >= 10
+    assert info["instances"] == 13 and info["items"] >= 13
     modes = [s[0] for s in info["shapes"]]
     # channel lanes for F <= 4; staged windows for F > 16 off the 16-byte grid (frame lanes
     # where a window exceeds the ring); frame lanes otherwise
