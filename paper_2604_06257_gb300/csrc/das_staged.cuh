@@ -184,7 +184,9 @@ __global__ void __launch_bounds__((NWC + 1) * 32) __maxnreg__(MAXR) k_das_staged
 
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int64_t tile = blockIdx.x;
+  // the last tiles (deepest rows of the grid, the widest apertures: the most pairs) start
+  // first, so that the light shallow tiles fill the tail of the launch
+  const int64_t tile = static_cast<int64_t>(gridDim.x) - 1 - blockIdx.x;
   const E* __restrict__ iq = static_cast<const E*>(p.iq);
   const size_t slab = static_cast<size_t>(p.S) * row_elems;
 

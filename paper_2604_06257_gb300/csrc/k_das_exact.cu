@@ -155,7 +155,9 @@ __global__ void __launch_bounds__((NWC + 1) * 32) __maxnreg__(MAXR) k_das_exact(
 
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int64_t tile = blockIdx.x;
+  // the last tiles (deepest rows of the grid, the widest apertures: the most pairs) start
+  // first, so that the light shallow tiles fill the tail of the launch
+  const int64_t tile = static_cast<int64_t>(gridDim.x) - 1 - blockIdx.x;
 
   if (threadIdx.x == 0) {
     for (int b = 0; b < NBUF; ++b) {
