@@ -58,7 +58,8 @@ __global__ void __launch_bounds__(NWARP * 32) k_das_frames(const DasParams p) {
   const int g = lane / FL;
   const int jl = lane % FL;
   const int f_base = blockIdx.y * FT;
-  const int64_t tile = blockIdx.x;
+  // deepest tiles (widest apertures, most terms) first: light tiles fill the launch's tail
+  const int64_t tile = static_cast<int64_t>(gridDim.x) - 1 - blockIdx.x;
   using E = typename IqStore<IQ>::E;
   const E* __restrict__ iq = static_cast<const E*>(p.iq);
   const int row_elems = p.F * IqStore<IQ>::eps;
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_das_channels(const DasParams p) 
   const int warp = threadIdx.x >> 5;
   const int g = lane / CL;
   const int jl = lane % CL;
-  const int64_t v = tile_voxel(p, blockIdx.x, warp * G + g);
+  const int64_t v = tile_voxel(p, static_cast<int64_t>(gridDim.x) - 1 - blockIdx.x, warp * G + g);
   const IQ* __restrict__ iq = static_cast<const IQ*>(p.iq);
   float2 acc[FMAX];
 #pragma unroll
