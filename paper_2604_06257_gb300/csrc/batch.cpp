@@ -238,7 +238,8 @@ mach_status mach_batch_plan(const mach_das_desc* descs, int32_t n, const mach_ti
     const double frames_slots = sh.mode == kBatchChannels ? 4.0 : (sh.mode == kBatchStaged ? 2.0 * sh.frame_lanes
                                                                                           : 4.0 * sh.frame_lanes);
     const double cost = static_cast<double>(voxels_per_block(sh)) * p.C * p.T * frames_slots;
-    for (int64_t t = 0; t < tiles; ++t) items.push_back({i, t, cost});
+    // an instance's deepest tiles (widest apertures) first, its shallow ones last
+    for (int64_t t = tiles - 1; t >= 0; --t) items.push_back({i, t, cost});
     b->points += static_cast<int64_t>(p.V) * p.C * p.T * p.F;
   }
   if (items.size() > static_cast<size_t>(INT32_MAX)) {
