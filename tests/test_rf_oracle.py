@@ -46,3 +46,33 @@ def test_analytic_echo_demodulates_to_the_iq_model():
     ref = iqm.simulate(acq, ph, seed=0, snr_db=None, accum=torch.complex128).numpy()
     err_db = 20 * np.log10(np.linalg.norm(d - ref) / np.linalg.norm(ref))
     assert err_db < -60.0, err_db
+
+
+def test_carrier_factors_into_complex_taps_and_an_output_rotation():
+    """The identity the polyphase RF kernel evaluates: with the carrier phase linear in the
+    sample index, exp(-j phase(nD + k - c)) = exp(-j phase(nD - c)) exp(-j 2 pi fc k / fs), so
+    filtering the real samples with complex taps h[k] exp(-j 2 pi fc k / fs) and rotating each
+    output once gives the mixed-then-filtered result; and the polyphase split k = qD + r sums
+    the same terms."""
+    r = np.random.default_rng(3)
+    rf = r.standard_normal((1, 2, 301, 3))
+    h = r.standard_normal(23)
+    fs, fc, t0, D = 83.2e6, 5.2e6, 0.9e-6, 4
+    ref = rf_oracle.rf_to_iq(rf, h, fs, fc, t0, D)
+    S, L = rf.shape[2], len(h)
+    c = (L - 1) // 2
+    n = np.arange((S - 1) // D + 1)
+    g = h * np.exp(-2j * np.pi * fc * np.arange(L) / fs)
+    P = -(-L // D)
+    out = np.zeros_like(ref)
+    for rr in range(D):                       # polyphase branches
+        for q in range(P):
+            k = q * D + rr
+            if k >= L:
+                continue
+            m = n * D + k - c
+            ok = (m >= 0) & (m < S)
+            out[:, :, ok, :] += g[k] * rf[:, :, m[ok], :]
+    out *= np.exp(-2j * np.pi * fc * (t0 + (n * D - c) / fs))[None, None, :, None]
+    np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-12)
+

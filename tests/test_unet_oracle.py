@@ -208,3 +208,28 @@ def test_coordinate_channels():
         fd = (f(p + e) - f(p - e)) / (2 * h)
         assert G[i] != 0.0
         assert G[i] == pytest.approx(fd, rel=2e-5, abs=1e-9), (tap, ci, co)
+
+
+def test_x_taps_folded_into_partial_sums_reproduce_the_convolution():
+    """The identity the x-folded tensor-core kernel evaluates: per (dz, dy) pair the three
+    x taps' partial sums P_j[x'] = sum_ci W[dz, dy, j - 1][ci] X[x', ci] on the unshifted x
+    positions, then Y[x] = P_0[x - 1] + P_1[x] + P_2[x + 1] (zero outside the volume), and
+    the mirrored shifts for the data gradient."""
+    r = np.random.default_rng(21)
+    x = r.standard_normal((1, 4, 5, 9, 16))
+    w = r.standard_normal((27, 16, 16))
+    xp = np.pad(x, ((0, 0), (1, 1), (1, 1), (1, 1), (0, 0)))
+    _, D, H, W, _ = x.shape
+    for flip in (False, True):
+        s = -1 if flip else 1
+        y = np.zeros(x.shape[:4] + (16,))
+        for pr in range(9):
+            dz, dy = s * (pr // 3 - 1), s * (pr % 3 - 1)
+            rows = xp[:, 1 + dz:1 + dz + D, 1 + dy:1 + dy + H, :, :]      # all x (with the zero border)
+            for j in range(3):
+                pj = rows @ w[3 * pr + j]                                  # P_j on x' = -1 .. W
+                dx = s * (j - 1)
+                y += pj[:, :, :, 1 + dx:1 + dx + W, :]
+        ref = U.conv3d_grad_input(x, np.transpose(w, (0, 2, 1))) if flip else U.conv3d(x, w)
+        np.testing.assert_allclose(y, ref, rtol=1e-12, atol=1e-12)
+
