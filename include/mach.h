@@ -318,7 +318,8 @@ mach_status mach_plan_device_status(mach_plan p, void *stream);
  * copy or launch (the runtime's last error is cleared).  Nothing is enqueued on argument
  * errors, when the tables do not fit or during a capture.
  * The first call on a device looks up the array's device address (do it before any
- * stream capture).  Calls share the array, so calls that overlap on the GPU race;
+ * stream capture) and keeps it for the life of the process: after cudaDeviceReset on that
+ * device the kept address is stale, so do not call this again in that process.  Calls share the array, so calls that overlap on the GPU race;
  * order them on one stream.  Returns after the host arrays are copied; the
  * beamforming itself is stream-ordered. */
 mach_status mach_das_run_noalloc(const mach_das_desc *d, const void *iq_dev, void *y_dev_or_null,

@@ -10,7 +10,8 @@
 //
 // The array's name is only a host-side stand-in in host code, so its device address is
 // fetched with cudaGetSymbolAddress, once per device, on the first call made with that
-// device current; that first call should therefore come before any stream capture.
+// device current; that first call should therefore come before any stream capture.  The
+// address is kept for the life of the process (a cudaDeviceReset would make it stale).
 // Every call reuses the same array and leaves the last call's tables in it: calls that
 // overlap on the GPU (different streams, or different host threads) race on it.  Each
 // call rewrites every table entry it reads, so nothing has to start at zero.
