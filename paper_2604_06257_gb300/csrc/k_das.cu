@@ -274,6 +274,9 @@ const VariantShape kShapes[] = {
     {"channels_c64_cl32",          1, 32,   1,    4,  kWarps, true,  false, 0, 8, 0},
     {"staged_c64p_x64_v4t16",      4, 16,   8,   64,  kWarps, false, true,  8, 8, 3, 16, true},
     {"staged_c64p_x64_v4t16e",     4, 16,   8,   64,  kWarps, false, true,  8, 8, 3, 16, true},
+    {"staged_c64p_x32_v4w7_t8x14", 4,  8,  16,   32,  7,      false, true,  4, 8, 3, 8, true, 8, 14},
+    {"staged_c64p_x32_f8v1w7_t8x7e", 8, 4,  8,   32,  7,      false, true,  8, 8, 3, 14, true, 8, 7},
+    {"staged_c64p_x64_v4_t8x8",    4, 16,   8,   64,  kWarps, false, true,  8, 8, 3, 16, true, 8, 8},
 };
 static_assert(sizeof(kShapes) / sizeof(kShapes[0]) == V_COUNT, "one shape row per variant");
 

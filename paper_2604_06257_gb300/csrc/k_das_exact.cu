@@ -332,7 +332,7 @@ cudaError_t launch_das_exact(const DasParams& p, Variant v, cudaStream_t s) {
   const size_t sm = exact_smem_bytes(v, p.rows_cap, p.T);
   switch (v) {
     //                                        FT FPL VPG NWC NBUF MAXR FLAGS
-    case V_SX32_C64P: return go_staged(k_das_exact<32, 4, 4, 7, 4, 64, 0>, 7, p, sm, s);
+    case V_SX32_C64P: case V_SX32_C64P_T8X14: return go_staged(k_das_exact<32, 4, 4, 7, 4, 64, 0>, 7, p, sm, s);
     case V_SX32_F4V2W7: return go_staged(k_das_exact<32, 4, 2, 7, 8, 64, 0>, 7, p, sm, s);
     case V_SX32_F8V1W7: return go_staged(k_das_exact<32, 8, 1, 7, 8, 64, 0>, 7, p, sm, s);
     case V_SX32_F4V2W15: return go_staged(k_das_exact<32, 4, 2, 15, 8, 64, 0>, 15, p, sm, s);
@@ -340,11 +340,12 @@ cudaError_t launch_das_exact(const DasParams& p, Variant v, cudaStream_t s) {
       return go_staged(k_das_exact<32, 8, 1, 15, 8, 64, 0>, 15, p, sm, s);
     case V_SX32_F8V1W15T24S: return go_staged(k_das_exact<32, 8, 1, 15, 8, 64, kSleep>, 15, p, sm, s);
     case V_SX32_F8V1W7T14: return go_staged(k_das_exact<32, 8, 1, 7, 8, 64, 0>, 7, p, sm, s);
-    case V_SX32_F8V1W7T14E: return go_staged(k_das_exact<32, 8, 1, 7, 8, 64, kEarly>, 7, p, sm, s);
+    case V_SX32_F8V1W7T14E: case V_SX32_F8V1W7_T8X7E:
+      return go_staged(k_das_exact<32, 8, 1, 7, 8, 64, kEarly>, 7, p, sm, s);
     case V_SX32_F4V2W7T14: return go_staged(k_das_exact<32, 4, 2, 7, 8, 64, 0>, 7, p, sm, s);
     case V_SX32_F8V1W15T30R12: return go_staged(k_das_exact<32, 8, 1, 15, 12, 64, 0>, 15, p, sm, s);
     case V_SX32_F8V1W15T30R12E: return go_staged(k_das_exact<32, 8, 1, 15, 12, 64, kEarly>, 15, p, sm, s);
-    case V_SX64_C64P: case V_SX64_C64P_T16:
+    case V_SX64_C64P: case V_SX64_C64P_T16: case V_SX64_C64P_T8X8:
       return go_staged(k_das_exact<64, 4, 4, 8, 8, 72, 0>, 8, p, sm, s);
     case V_SX64_C64P_T16E: return go_staged(k_das_exact<64, 4, 4, 8, 8, 72, kEarly>, 8, p, sm, s);
     case V_SX64_C64PS: return go_staged(k_das_exact<64, 4, 4, 8, 8, 72, kSleep>, 8, p, sm, s);

@@ -70,6 +70,10 @@ enum Variant : int32_t {
   V_CH_C64_L32,      // channel lanes, F <= 4, complex64, 32 lanes per voxel
   V_SX64_C64P_T16,   // as V_SX64_C64P with 16 x 4 voxel tiles (2D)
   V_SX64_C64P_T16E,  // as V_SX64_C64P_T16, ring slots released per pair
+  V_SX32_C64P_T8X14,    // as V_SX32_C64P with one-plane 8 x 14 x 1 tiles on 3D grids
+  V_SX32_F8V1W7_T8X7E,  // 8 frames x 1 voxel per lane, 7 consumer warps, 8 x 7 x 1 tiles on
+                        // 3D grids (14 x 4 in 2D), ring slots released per pair
+  V_SX64_C64P_T8X8,     // as V_SX64_C64P with one-plane 8 x 8 x 1 tiles on 3D grids
   V_COUNT
 };
 
@@ -87,6 +91,8 @@ struct VariantShape {
   int iq_type;           // mach_iq_dtype the variant reads
   int tile2d_x;          // 2D tile width (0: squarest power-of-two split)
   bool exact_frames;     // serves only F == frame_tile (k_das_exact.cu)
+  int tile3d_x;          // 3D tile width and height (the rest along z; 0: pick_tile's box)
+  int tile3d_y;
 };
 
 const VariantShape& variant_shape(Variant v);

@@ -171,10 +171,10 @@ Variant unstaged(Variant v) {
     case V_ST32_C64P_V4: case V_ST32_C64P_V4W7: case V_SX32_C64P: case V_SX32_F4V2W7: case V_SX32_F8V1W7:
     case V_SX32_F4V2W15: case V_SX32_F8V1W15: case V_SX32_F8V1W15T24: case V_SX32_F8V1W15T40:
     case V_SX32_F8V1W15T24S: case V_SX32_F8V1W7T14: case V_SX32_F8V1W7T14E: case V_SX32_F4V2W7T14:
-    case V_SX32_F8V1W15T30R12: case V_SX32_F8V1W15T30R12E:
+    case V_SX32_F8V1W15T30R12: case V_SX32_F8V1W15T30R12E: case V_SX32_C64P_T8X14: case V_SX32_F8V1W7_T8X7E:
       return V_F32_C64P;
     case V_ST64_C64P_V4: case V_SX64_C64P: case V_SX64_F8V2: case V_SX64_C64PS: case V_SX64_C64PE:
-    case V_SX64_C64P_T16: case V_SX64_C64P_T16E:
+    case V_SX64_C64P_T16: case V_SX64_C64P_T16E: case V_SX64_C64P_T8X8:
       return V_F64_C64P;
     case V_SX16_F4V2W7: case V_SX16_F4V1W7: case V_SX8_F4V1W7: return V_F32_C64P;
     case V_ST64_B16_V4: return V_F64_B16;
@@ -201,7 +201,7 @@ Variant staged_fallback(Variant v) {
     case V_ST64_H16_V4: return V_ST64_H16;
     case V_SX32_F8V1W15: case V_SX32_F4V2W15: case V_SX32_F8V1W7: case V_SX32_F4V2W7: case V_SX32_F8V1W15T24:
     case V_SX32_F8V1W15T40: case V_SX32_F8V1W15T24S: case V_SX32_F8V1W7T14: case V_SX32_F8V1W7T14E:
-    case V_SX32_F4V2W7T14: case V_SX32_F8V1W15T30R12: case V_SX32_F8V1W15T30R12E:
+    case V_SX32_F4V2W7T14: case V_SX32_F8V1W15T30R12: case V_SX32_F8V1W15T30R12E: case V_SX32_F8V1W7_T8X7E:
       return V_SX32_C64P;
     default: return v;
   }
@@ -214,9 +214,10 @@ Variant generic_staged(Variant v) {
     case V_SX32_C64P: case V_SX32_F4V2W7: case V_SX32_F8V1W7: case V_SX32_F4V2W15: case V_SX32_F8V1W15:
     case V_SX32_F8V1W15T24: case V_SX32_F8V1W15T40: case V_SX32_F8V1W15T24S: case V_SX32_F8V1W7T14:
     case V_SX32_F8V1W7T14E: case V_SX32_F4V2W7T14: case V_SX32_F8V1W15T30R12: case V_SX32_F8V1W15T30R12E:
+    case V_SX32_C64P_T8X14: case V_SX32_F8V1W7_T8X7E:
       return V_ST32_C64P_V4W7;
     case V_SX64_C64P: case V_SX64_F8V2: case V_SX64_C64PS: case V_SX64_C64PE: case V_SX64_C64P_T16:
-    case V_SX64_C64P_T16E:
+    case V_SX64_C64P_T16E: case V_SX64_C64P_T8X8:
       return V_ST64_C64P_V4;
     case V_SX16_F4V2W7: case V_SX16_F4V1W7: case V_SX8_F4V1W7: return V_F32_C64P;
     default: return v;
@@ -298,6 +299,11 @@ static mach_status configure_tiles(DasParams& b, Variant var, bool list, int64_t
     tile[0] = shp.tile2d_x;
     tile[1] = 1;
     tile[2] = per_cta / shp.tile2d_x;
+  }
+  if (shp.tile3d_x && !list && b.ny > 1 && per_cta % (shp.tile3d_x * shp.tile3d_y) == 0) {
+    tile[0] = shp.tile3d_x;
+    tile[1] = shp.tile3d_y;
+    tile[2] = per_cta / (shp.tile3d_x * shp.tile3d_y);
   }
   if (tile[0] * tile[1] * tile[2] != per_cta) return MACH_ERR_UNSUPPORTED;   // slots must map 1:1
   b.tile_x = tile[0];
@@ -418,9 +424,12 @@ mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) 
                          : static_cast<int64_t>(d->grid_dims[0]) * d->grid_dims[1] * d->grid_dims[2];
   if (list && V > INT32_MAX) return MACH_ERR_UNSUPPORTED;
   Variant var = pick_variant(d->iq_dtype, F);
-  // 3D grids with 32 frames: the exact kernel's 112-voxel 3D tiles (4 frames per lane) beat
-  // its shallow 14 x 4 tiles (94 x 94 x 178 voxels, 1024 elements: 2.29 against 2.10 T points/s)
-  if (var == V_SX32_F8V1W7T14E && !list && d->grid_dims[1] > 1) var = V_SX32_C64P;
+  // 3D grids with 32 frames: one-plane 8 x 7 x 1 tiles.  A voxel step in depth moves the
+  // two-way delay by about two samples per sample-unit of step, a lateral step by far less,
+  // so a tile one plane deep has the shortest sample windows per voxel (94 x 94 x 178 voxels,
+  // 1024 elements: 2.82 T points/s, against 2.31 for 8 x 2 x 7 tiles at 4 frames per lane
+  // and 2.10 for 8 x 1 x 7 tiles at 8)
+  if (var == V_SX32_F8V1W7T14E && !list && d->grid_dims[1] > 1) var = V_SX32_F8V1W7_T8X7E;
   // 2D grids with 64 frames: shallow 16 x 4 tiles keep the windows short enough for the
   // 8-slot ring of 512-byte rows (the squarest 8 x 8 tiles do not fit; the L1 path then
   // ran 256 x 256 px at 1.47 against 2.11 T points/s)

@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 # (default exact-frame variant, the generic variant it specialises), per frame count; 3D
 # grids with 32 frames default to the exact kernel with 3D tiles of 112 voxels
 PAIRS = {32: ("staged_c64p_x32_f8v1w7t14e", "staged_c64p_ft32_v4w7"), 64: ("staged_c64p_x64_v4", "staged_c64p_ft64_v4")}
-PAIRS_3D = {32: ("staged_c64p_x32_v4w7", "staged_c64p_ft32_v4w7"), 64: PAIRS[64]}
+PAIRS_3D = {32: ("staged_c64p_x32_f8v1w7_t8x7e", "staged_c64p_ft32_v4w7"), 64: PAIRS[64]}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -84,13 +84,39 @@ def test_exact_equals_generic_bitwise_small(name):
     print(name, check_oracle(acq, iq, y_x, pd_x))
 
 
-def test_exact_3d_32_frames_defaults_to_3d_tiles():
-    """3D grid, 32 frames: the default is the exact kernel with 3D tiles of 112 voxels,
-    bitwise equal to the generic kernel and within the oracle bars."""
+def test_exact_3d_32_frames_defaults_to_one_plane_tiles():
+    """3D grid, 32 frames: the default is the exact kernel with one-plane 8 x 7 x 1 tiles
+    (8 frames per lane), bitwise equal to the generic kernel and within the oracle bars."""
     acq = synth.make_acquisition("ulm3d", "small").replace(n_frames=32)
     iq = synth.random_iq(acq, 33)
     (y_x, pd_x, _), _ = run_both(acq, iq)
     print(check_oracle(acq, iq, y_x, pd_x))
+
+
+@pytest.mark.parametrize("name,tile", [("staged_c64p_x32_v4w7_t8x14", [8, 14, 1]),
+                                       ("staged_c64p_x32_f8v1w7_t8x7e", [8, 7, 1]),
+                                       ("staged_c64p_x64_v4_t8x8", [8, 8, 1])])
+def test_exact_one_plane_3d_tiles(name, tile):
+    """3D grids in one-plane tiles (ragged in x and y): the frames are bitwise those of the
+    generic kernel and within the oracle bars."""
+    F = 64 if "_x64_" in name else 32
+    acq = synth.make_acquisition("ulm3d", "small").replace(n_frames=F, iq_dtype="c64split")
+    iq = synth.random_iq(acq, 35 + F)
+    x = synth.iqmod.to_c64split(iq.cuda())
+    kw = m.plan_kwargs(acq)
+    out = []
+    for v in (name, PAIRS_3D[F][1]):
+        with forced(kw, v) as p:
+            info = p.info()
+            assert info["variant"] == v
+            if v == name:
+                assert info["tile"] == tile
+            pd, y = p.power_doppler(x, want_y=True)
+            torch.cuda.synchronize()
+            assert p.device_status() == m.MACH_OK
+            out.append((y, pd, info["frames_per_lane"]))
+    same_bits(*out)
+    print(name, check_oracle(acq, iq, out[0][0], out[0][1]))
 
 
 def test_exact_2d_64_frames_shallow_tiles():
@@ -217,7 +243,8 @@ SHAPES = [("staged_c64p_x32_v4w7", 32), ("staged_c64p_x32_f4v2w7", 32), ("staged
           ("staged_c64p_x32_f8v1w15t24s", 32), ("staged_c64p_x64_v4s", 64), ("staged_c64p_x32_f8v1w7t14", 32),
           ("staged_c64p_x32_f8v1w7t14e", 32), ("staged_c64p_x32_f4v2w7t14", 32), ("staged_c64p_x32_f8v1w15t30r12", 32),
           ("staged_c64p_x32_f8v1w15t30r12e", 32), ("staged_c64p_x64_v4e", 64), ("staged_c64p_x64_v4t16", 64),
-          ("staged_c64p_x64_v4t16e", 64)]
+          ("staged_c64p_x64_v4t16e", 64), ("staged_c64p_x32_v4w7_t8x14", 32), ("staged_c64p_x32_f8v1w7_t8x7e", 32),
+          ("staged_c64p_x64_v4_t8x8", 64)]
 
 
 @pytest.mark.parametrize("name,F", SHAPES)
