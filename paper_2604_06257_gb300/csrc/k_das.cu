@@ -277,6 +277,8 @@ const VariantShape kShapes[] = {
     {"staged_c64p_x32_v4w7_t8x14", 4,  8,  16,   32,  7,      false, true,  4, 8, 3, 8, true, 8, 14},
     {"staged_c64p_x32_f8v1w7_t8x7e", 8, 4,  8,   32,  7,      false, true,  8, 8, 3, 14, true, 8, 7},
     {"staged_c64p_x64_v4_t8x8",    4, 16,   8,   64,  kWarps, false, true,  8, 8, 3, 16, true, 8, 8},
+    {"staged_c64p_x16_f4v2w7_t8x14", 4, 4, 16,   16,  7,      false, true,  8, 8, 3, 28, true, 8, 14},
+    {"staged_c64p_x8_f4v1w7_t8x14", 4,  2,  16,    8,  7,      false, true,  8, 8, 3, 28, true, 8, 14},
 };
 static_assert(sizeof(kShapes) / sizeof(kShapes[0]) == V_COUNT, "one shape row per variant");
 

@@ -351,9 +351,10 @@ cudaError_t launch_das_exact(const DasParams& p, Variant v, cudaStream_t s) {
     case V_SX64_C64PS: return go_staged(k_das_exact<64, 4, 4, 8, 8, 72, kSleep>, 8, p, sm, s);
     case V_SX64_C64PE: return go_staged(k_das_exact<64, 4, 4, 8, 8, 72, kEarly>, 8, p, sm, s);
     case V_SX64_F8V2: return go_staged(k_das_exact<64, 8, 2, 8, 8, 72, 0>, 8, p, sm, s);
-    case V_SX16_F4V2W7: return go_staged(k_das_exact<16, 4, 2, 7, 8, 64, kEarly>, 7, p, sm, s);
+    case V_SX16_F4V2W7: case V_SX16_F4V2W7_T8X14:
+      return go_staged(k_das_exact<16, 4, 2, 7, 8, 64, kEarly>, 7, p, sm, s);
     case V_SX16_F4V1W7: return go_staged(k_das_exact<16, 4, 1, 7, 8, 64, kEarly>, 7, p, sm, s);
-    case V_SX8_F4V1W7: return go_staged(k_das_exact<8, 4, 1, 7, 8, 64, kEarly>, 7, p, sm, s);
+    case V_SX8_F4V1W7: case V_SX8_F4V1W7_T8X14: return go_staged(k_das_exact<8, 4, 1, 7, 8, 64, kEarly>, 7, p, sm, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -74,6 +74,8 @@ enum Variant : int32_t {
   V_SX32_F8V1W7_T8X7E,  // 8 frames x 1 voxel per lane, 7 consumer warps, 8 x 7 x 1 tiles on
                         // 3D grids (14 x 4 in 2D), ring slots released per pair
   V_SX64_C64P_T8X8,     // as V_SX64_C64P with one-plane 8 x 8 x 1 tiles on 3D grids
+  V_SX16_F4V2W7_T8X14,  // as V_SX16_F4V2W7 with one-plane 8 x 14 x 1 tiles on 3D grids
+  V_SX8_F4V1W7_T8X14,   // as V_SX8_F4V1W7 with one-plane 8 x 14 x 1 tiles on 3D grids
   V_COUNT
 };
 

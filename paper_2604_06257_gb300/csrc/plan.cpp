@@ -176,7 +176,8 @@ Variant unstaged(Variant v) {
     case V_ST64_C64P_V4: case V_SX64_C64P: case V_SX64_F8V2: case V_SX64_C64PS: case V_SX64_C64PE:
     case V_SX64_C64P_T16: case V_SX64_C64P_T16E: case V_SX64_C64P_T8X8:
       return V_F64_C64P;
-    case V_SX16_F4V2W7: case V_SX16_F4V1W7: case V_SX8_F4V1W7: return V_F32_C64P;
+    case V_SX16_F4V2W7: case V_SX16_F4V1W7: case V_SX8_F4V1W7: case V_SX16_F4V2W7_T8X14: case V_SX8_F4V1W7_T8X14:
+      return V_F32_C64P;
     case V_ST64_B16_V4: return V_F64_B16;
     default: return v;
   }
@@ -219,7 +220,8 @@ Variant generic_staged(Variant v) {
     case V_SX64_C64P: case V_SX64_F8V2: case V_SX64_C64PS: case V_SX64_C64PE: case V_SX64_C64P_T16:
     case V_SX64_C64P_T16E: case V_SX64_C64P_T8X8:
       return V_ST64_C64P_V4;
-    case V_SX16_F4V2W7: case V_SX16_F4V1W7: case V_SX8_F4V1W7: return V_F32_C64P;
+    case V_SX16_F4V2W7: case V_SX16_F4V1W7: case V_SX8_F4V1W7: case V_SX16_F4V2W7_T8X14: case V_SX8_F4V1W7_T8X14:
+      return V_F32_C64P;
     default: return v;
   }
 }

@@ -93,19 +93,24 @@ def test_exact_3d_32_frames_defaults_to_one_plane_tiles():
     print(check_oracle(acq, iq, y_x, pd_x))
 
 
-@pytest.mark.parametrize("name,tile", [("staged_c64p_x32_v4w7_t8x14", [8, 14, 1]),
-                                       ("staged_c64p_x32_f8v1w7_t8x7e", [8, 7, 1]),
-                                       ("staged_c64p_x64_v4_t8x8", [8, 8, 1])])
-def test_exact_one_plane_3d_tiles(name, tile):
-    """3D grids in one-plane tiles (ragged in x and y): the frames are bitwise those of the
-    generic kernel and within the oracle bars."""
-    F = 64 if "_x64_" in name else 32
+ONE_PLANE = [("staged_c64p_x32_v4w7_t8x14", "staged_c64p_ft32_v4w7", [8, 14, 1], 32),
+             ("staged_c64p_x32_f8v1w7_t8x7e", "staged_c64p_ft32_v4w7", [8, 7, 1], 32),
+             ("staged_c64p_x64_v4_t8x8", "staged_c64p_ft64_v4", [8, 8, 1], 64),
+             ("staged_c64p_x16_f4v2w7_t8x14", "staged_c64p_x16_f4v2w7", [8, 14, 1], 16),
+             ("staged_c64p_x8_f4v1w7_t8x14", "staged_c64p_x8_f4v1w7", [8, 14, 1], 8)]
+
+
+@pytest.mark.parametrize("name,base,tile,F", ONE_PLANE)
+def test_exact_one_plane_3d_tiles(name, base, tile, F):
+    """3D grids in one-plane tiles (ragged in x and y): each voxel's kept terms arrive in
+    the same pair order as with any other tiling, so the frames are bitwise those of the
+    same kernel on its own tiles (or of the generic kernel), and within the oracle bars."""
     acq = synth.make_acquisition("ulm3d", "small").replace(n_frames=F, iq_dtype="c64split")
     iq = synth.random_iq(acq, 35 + F)
     x = synth.iqmod.to_c64split(iq.cuda())
     kw = m.plan_kwargs(acq)
     out = []
-    for v in (name, PAIRS_3D[F][1]):
+    for v in (name, base):
         with forced(kw, v) as p:
             info = p.info()
             assert info["variant"] == v
@@ -117,6 +122,21 @@ def test_exact_one_plane_3d_tiles(name, tile):
             out.append((y, pd, info["frames_per_lane"]))
     same_bits(*out)
     print(name, check_oracle(acq, iq, out[0][0], out[0][1]))
+
+
+@pytest.mark.parametrize("F,expect", [(8, "staged_c64p_x8_f4v1w7"), (16, "staged_c64p_x16_f4v2w7")])
+def test_exact_3d_short_ensembles_keep_their_3d_tiles(F, expect):
+    """3D grids with 8 or 16 frames keep 8 x 2 x 7 tiles (one-plane tiles measured no faster
+    for these frame counts)."""
+    acq = synth.make_acquisition("ulm3d", "small").replace(n_frames=F, iq_dtype="c64split")
+    iq = synth.random_iq(acq, 45 + F)
+    with m.Plan(**m.plan_kwargs(acq)) as p:
+        info = p.info()
+        assert info["variant"] == expect and info["tile"] == [8, 2, 7]
+        pd, y = p.power_doppler(synth.iqmod.to_c64split(iq.cuda()), want_y=True)
+        torch.cuda.synchronize()
+        assert p.device_status() == m.MACH_OK
+    print(F, check_oracle(acq, iq, y, pd))
 
 
 def test_exact_2d_64_frames_shallow_tiles():
