@@ -426,9 +426,10 @@ mach_status mach_das_plan(const mach_das_desc* d, void* stream, mach_plan* out) 
                          : static_cast<int64_t>(d->grid_dims[0]) * d->grid_dims[1] * d->grid_dims[2];
   if (list && V > INT32_MAX) return MACH_ERR_UNSUPPORTED;
   Variant var = pick_variant(d->iq_dtype, F);
-  // 3D grids with 32 frames: one-plane 8 x 7 x 1 tiles.  A voxel step in depth moves the
-  // two-way delay by about two samples per sample-unit of step, a lateral step by far less,
-  // so a tile one plane deep has the shortest sample windows per voxel (94 x 94 x 178 voxels,
+  // 3D grids with 32 frames: one-plane 8 x 7 x 1 tiles.  A step in depth moves the two-way
+  // delay about twice as far as the step itself, a lateral step far less, so a tile one
+  // plane deep needs the shortest sample windows; with 256-byte rows that shrinks the ring
+  // (15 instead of 36 rows a slot) and more blocks stay resident (94 x 94 x 178 voxels,
   // 1024 elements: 2.82 T points/s, against 2.31 for 8 x 2 x 7 tiles at 4 frames per lane
   // and 2.10 for 8 x 1 x 7 tiles at 8)
   if (var == V_SX32_F8V1W7T14E && !list && d->grid_dims[1] > 1) var = V_SX32_F8V1W7_T8X7E;
