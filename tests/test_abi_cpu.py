@@ -191,3 +191,34 @@ def test_rf_to_iq_size_limits_refused_before_launch():
     # more than 2^24 frames (a block's outputs are counted in 32 bits)
     assert L.mach_rf_to_iq(fake, fake, 1, 1, 100, (1 << 24) + 1, 20e6, 5e6, 0.0, h.ctypes.data, 8, 1,
                            None) == m.MACH_ERR_UNSUPPORTED
+
+
+def test_every_variant_name_the_tests_force_is_known():
+    """Each kernel variant the GPU tests, the benchmark or the autotuner name by string is
+    one the library knows (the lookup needs no GPU); an unknown name is refused."""
+    pat = re.compile(r"[\"']((?:staged|frames|channels)_(?:c64p|c64|f16|b16|h16)_[a-z0-9_]+)[\"']")
+    names = set()
+    for rel in ("tests", "paper_2604_06257_gb300"):
+        d = os.path.join(ROOT, rel)
+        for f in sorted(os.listdir(d)):
+            if f.endswith(".py"):
+                names |= set(pat.findall(open(os.path.join(d, f)).read()))
+    names |= set(pat.findall(open(os.path.join(ROOT, "bench.py")).read()))
+    assert len(names) > 30
+    unknown = []
+    try:
+        for n in sorted(names):
+            try:
+                m.mach_debug_force_variant(n)
+            except m.MachError:
+                unknown.append(n)
+        known = names - set(unknown)
+        # the rest are families matched with startswith ("staged_c64p_x32")
+        for n in unknown:
+            assert any(k.startswith(n + "_") for k in known), n
+        assert len(unknown) <= 2
+        with pytest.raises(m.MachError) as e:
+            m.mach_debug_force_variant("staged_no_such_variant")
+        assert e.value.status == m.MACH_ERR_INVALID_ARG
+    finally:
+        m.mach_debug_force_variant(None)
