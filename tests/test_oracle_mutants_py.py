@@ -4,6 +4,7 @@ Each case plants one mistake in a copy of the oracle's source (a wrong slope, a 
 factor, a transposed operand, a swapped concatenation, a dropped bias correction, a wrong
 sign or index), loads it as a separate module, swaps it in for the real one and runs the
 pins; at least one pin must fail.  The real oracle is untouched."""
+import inspect
 import os
 import sys
 import types
@@ -33,6 +34,10 @@ def _mutant(rel, old, new, tag):
 
 
 def _caught(pin_module, attr, mutant, pins):
+    # every pin must run without arguments: a parametrised pin would raise for want of them
+    # and count every mutant as caught
+    for fn in pins:
+        assert not inspect.signature(fn).parameters, fn.__name__
     real = getattr(pin_module, attr)
     setattr(pin_module, attr, mutant)
     try:
@@ -80,6 +85,8 @@ RF_MUTANTS = [
     ("carrier drops t0", "(t0 + m / fs))[None, None, :, None]", "(m / fs))[None, None, :, None]"),
     ("filter not centred", "c = (len(h) - 1) // 2", "c = 0"),
     ("decimation ignored", "idx = n * decim + k - c", "idx = n + k - c"),
+    ("taps reversed", "out[:, :, ok, :] += h[k] * b[:, :, idx[ok], :]", "out[:, :, ok, :] += h[len(h) - 1 - k] * b[:, :, idx[ok], :]"),
+    ("centre rounded up", "c = (len(h) - 1) // 2", "c = len(h) // 2"),
 ]
 RF_PINS = [getattr(rf_pins, n) for n in dir(rf_pins) if n.startswith("test_")]
 

@@ -76,3 +76,26 @@ def test_carrier_factors_into_complex_taps_and_an_output_rotation():
     out *= np.exp(-2j * np.pi * fc * (t0 + (n * D - c) / fs))[None, None, :, None]
     np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-12)
 
+
+
+def test_centred_fir_equals_library_correlation():
+    """The filter and decimation steps against numpy's correlation: with the mixed samples
+    zero-padded by c = (L - 1) // 2 in front and L - 1 - c behind, the 'valid' correlation
+    with the taps at index nD is the centred FIR output n (odd and even tap counts, one tap,
+    several decimations)."""
+    fs, fc, t0 = 31.2e6, 7.8e6, 0.4e-6
+    m = np.arange(57)
+    for L, D in ((7, 1), (8, 3), (1, 2), (12, 5)):
+        r = np.random.default_rng(10 + L + D)
+        rf = r.standard_normal((2, 3, 57, 2))
+        h = r.standard_normal(L)
+        out = rf_oracle.rf_to_iq(rf, h, fs, fc, t0, D)
+        b = rf * np.exp(-2j * np.pi * fc * (t0 + m / fs))[None, None, :, None]
+        c = (L - 1) // 2
+        assert out.shape == (2, 3, (57 - 1) // D + 1, 2)
+        for t in range(2):
+            for ch in range(3):
+                for f in range(2):
+                    bp = np.concatenate([np.zeros(c), b[t, ch, :, f], np.zeros(L - 1 - c)])
+                    ref = np.correlate(bp, h, mode="valid")[::D]
+                    np.testing.assert_allclose(out[t, ch, :, f], ref, rtol=1e-12, atol=1e-12)
