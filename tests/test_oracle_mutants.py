@@ -38,6 +38,14 @@ MUTANTS = [
     ("contract rx drops dy", "float rx = sqrtf(fmaf(fdx, fdx, fmaf(fdy, fdy, fdz * fdz)));",
      "float rx = sqrtf(fmaf(fdx, fdx, fdz * fdz));"),
     ("channel stride", "(((int64_t)t * C + c) * S + tm.i0)", "(((int64_t)c * T + t) * S + tm.i0)"),
+    ("hann not squared", "double cp = cos(M_PI * t); return cp * cp;", "double cp = cos(M_PI * t); return cp;"),
+    ("gauss of t, not t squared", "exp(-8.0 * t * t)", "exp(-8.0 * t)"),
+    ("window argument drops F#", "rho * d->f_number / dz", "rho / dz"),
+    ("aperture edge excluded", "rho * 2.0 * d->f_number <= dz", "rho * 2.0 * d->f_number < dz"),
+    ("contract keeps elements behind the voxel", "(fdz > 0.0f && frho2", "(fdz != 0.0f && frho2"),
+    ("contract aperture drops dy", "float frho2 = fmaf(fdx, fdx, fdy * fdy);", "float frho2 = fdx * fdx;"),
+    ("index rounded up", "double fl = floor(s);", "double fl = ceil(s);"),
+    ("power averaged over frames", "if (pd) pd[j] = pw;", "if (pd) pd[j] = pw / F;"),
 ]
 
 PINS = [
@@ -61,6 +69,9 @@ PINS = [
     (pins.test_brute_force_tiny_random, dict(seed=2)),
     (pins.test_brute_force_tiny_random, dict(seed=3)),
     (pins.test_brute_force_small_workloads, {}),
+    (pins.test_voxels_behind_the_array_get_no_terms, dict(mode="exact")),
+    (pins.test_voxels_behind_the_array_get_no_terms, dict(mode="contract")),
+    (pins.test_contract_decisions_match_exact_in_3d, {}),
 ]
 
 

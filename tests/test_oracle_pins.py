@@ -203,6 +203,45 @@ def test_apod_none_has_no_mask():
     assert tr["i0"][1, 0, 0] == -1 or tr["valid"][1, 0, 0] == (tr["s"][1, 0, 0] >= 0)
 
 
+@pytest.mark.parametrize("mode", ["exact", "contract"])
+def test_voxels_behind_the_array_get_no_terms(mode):
+    """R6: an element contributes only to voxels in front of it (dz > 0), whatever the
+    window.  t0 < 0 puts voxels behind the array plane inside the sample range, so only the
+    aperture rule can drop them (on axis the squared test alone would keep them)."""
+    for apod in ("boxcar", "hann", "gauss"):
+        acq = one_element([-10e-3, -2e-3, -0.5e-3], x_list=[0.0, 0.5e-3, 0.0], apod=apod, S=256,
+                          t0=-30e-6)
+        tr = oracle.terms(acq, mode=mode)
+        assert (tr["i0"] >= 0).all()                 # in range: the aperture decides
+        assert not tr["valid"].any()
+
+
+def test_contract_decisions_match_exact_in_3d():
+    """On a 3D grid (matrix array, waves steered in azimuth and in elevation) the contract
+    mode keeps the same terms as the exact mode, except within float rounding of the
+    aperture edge or of the range ends, and its window values agree to float precision."""
+    acq = synth.volume3d(n=12, n_frames=1, n_side=16, n_samples=512).replace(
+        grid_origin=(-1.6137e-3, -1.6291e-3, 1.5173e-3), grid_step=(3e-4, 3e-4, 3e-4))
+    # shallow, so the aperture cuts; the grid is off the element lattice, so few terms sit
+    # exactly on an aperture edge (on the lattice, rho 2F# = dz happens exactly)
+    idx = np.arange(0, acq.n_vox, 3)
+    te = oracle.terms(acq, idx, mode="exact")
+    tc = oracle.terms(acq, idx, mode="contract")
+    p = acq.voxel_positions()[idx].astype(np.float64)
+    e = acq.elem_pos.astype(np.float64)
+    d = p[:, None, :] - e[None, :, :]
+    rho = np.sqrt(d[..., 0] ** 2 + d[..., 1] ** 2)
+    dz = d[..., 2]
+    edge = np.abs(2.0 * acq.f_number * rho - dz) <= 1e-5 * np.abs(dz)      # [n, C]
+    ends = np.minimum(np.abs(te["s"]), np.abs(te["s"] - (acq.n_samples - 1))) < 1e-3
+    diff = te["valid"] != tc["valid"]
+    assert te["valid"].sum() > 1000 and (~te["valid"]).sum() > 1000       # both kinds present
+    assert not (diff & ~(edge[:, :, None] | ends)).any()
+    assert diff.sum() <= 1e-3 * diff.size
+    both = te["valid"] & tc["valid"]
+    assert np.max(np.abs(te["a"][both] - tc["a"][both])) < 1e-5
+
+
 # ------------------------------------------------- point scatterer ----
 
 @pytest.mark.parametrize("apod", ["none", "hann"])
