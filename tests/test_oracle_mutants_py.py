@@ -70,6 +70,15 @@ UNET_MUTANTS = [
     ("skip gradient slice", 'c_up = spec[dec(l, 0)].ci - A[f"e{l}"].shape[-1]', 'c_up = A[f"e{l}"].shape[-1]'),
     ("bias gradient summed over channels", "G[s.b_off:s.b_off + s.co] += gz.reshape(-1, s.co).sum(axis=0)",
      "G[s.b_off:s.b_off + s.co] += gz.reshape(-1, s.co).sum()"),
+    ("pooling takes the maximum", "2, W // 2, 2, C).mean(axis=(2, 4, 6))", "2, W // 2, 2, C).max(axis=(2, 4, 6))"),
+    ("bias left out of the forward pass", "    if b is not None:\n        y += b", "    if b is not None:\n        y += 0.0 * b"),
+    ("second moment of |g|", "v = beta2 * v + (1 - beta2) * g * g", "v = beta2 * v + (1 - beta2) * np.abs(g)"),
+    ("epsilon inside the root", "(np.sqrt(vh) + eps)", "np.sqrt(vh + eps)"),
+    ("coordinates not centred", "(2.0 * np.arange(n) + 1.0 - n) / P", "(2.0 * np.arange(n) - n) / P"),
+    ("rms over all volumes of a batch", "ms = (np.abs(y) ** 2).mean(axis=0)", "ms = np.full(y.shape[1], (np.abs(y) ** 2).mean())"),
+    ("upsampling shifted by a voxel",
+     "def up2(x):\n    return np.repeat(np.repeat(np.repeat(x, 2, axis=1), 2, axis=2), 2, axis=3)",
+     "def up2(x):\n    return np.roll(np.repeat(np.repeat(np.repeat(x, 2, axis=1), 2, axis=2), 2, axis=3), 1, axis=3)"),
 ]
 UNET_PINS = [getattr(unet_pins, n) for n in dir(unet_pins) if n.startswith("test_")]
 
