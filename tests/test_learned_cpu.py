@@ -55,3 +55,30 @@ def test_gain_and_error_measure():
     assert Lc.nrmse_db(ref * 1.1, ref) == pytest.approx(20 * math.log10(0.1), abs=1e-4)
     x, t = Lc.compose(Lc.Bank(few, 2 * few, [], 4), torch.eye(6, 2, dtype=torch.complex64))
     assert torch.equal(x, few[:, :2]) and torch.equal(t, 2 * few[:, :2])
+
+
+def test_wiener_bound_closed_forms():
+    """The error floor of the bound study, E(lam) = sum_k [S_MM - |S_MF|^2 / (S_FF + lam max S_FF)]
+    / sum_k S_MM, on cases with a closed form: identical images -> E = lam / (1 + lam) per
+    frequency; uncorrelated images -> 0 dB; one frequency seen at two sub-voxel positions whose
+    few/many phases differ by delta -> |S_MF|^2 = cos^2(delta / 2), E = sin^2(delta / 2) as
+    lam -> 0; and the frequencies weigh in by their S_MM."""
+    from paper_2604_06257_gb300 import learned_bound as B
+    rng = np.random.default_rng(0)
+    h = rng.standard_normal(50) + 1j * rng.standard_normal(50)
+    p = np.abs(h) ** 2
+    same = B.floor_db(p, p, p, lams=(1e-2, 1e-4))
+    s = np.sum(p * (1e-2 * p.max()) / (p + 1e-2 * p.max())) / p.sum()
+    assert same["0.01"] == pytest.approx(10 * math.log10(s), abs=1e-9)
+    assert same["0.0001"] < same["0.01"] - 15
+    assert B.floor_db(p, p, np.zeros(50), lams=(1e-3,))["0.001"] == pytest.approx(0.0, abs=1e-12)
+    for delta in (0.3, 1.0, 2.5):
+        F = np.array([1.0, np.exp(1j * 0.7)])             # the FEW image at two positions
+        M = np.array([1.0, np.exp(1j * (0.7 + delta))])   # the MANY image, phase moved by delta
+        sff, smm, smf = np.mean(np.abs(F) ** 2), np.mean(np.abs(M) ** 2), np.mean(M * F.conj())
+        e = B.floor_db(np.array([sff]), np.array([smm]), np.array([smf]), lams=(1e-12,))["1e-12"]
+        assert e == pytest.approx(10 * math.log10(math.sin(delta / 2) ** 2), abs=1e-6)
+    # two frequencies, one perfectly predictable (weight 3), one not (weight 1): E = 1/4
+    e = B.floor_db(np.array([1.0, 1.0]), np.array([3.0, 1.0]), np.array([math.sqrt(3.0), 0.0]),
+                   lams=(1e-12,))["1e-12"]
+    assert e == pytest.approx(10 * math.log10(0.25), abs=1e-6)
