@@ -73,7 +73,8 @@ def parse():
     ap.add_argument("--iq-dtype", default="c64split", choices=["c64", "f16x2", "bf16x2", "c64split"],
                     help="IQ storage the timed kernel reads (prepared by K0 outside the timed region)")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the other workloads (volume3d, bmode2d, ragged batch) reported beside the headline")
+                    help="skip the other workloads (volume3d, bmode2d, ragged batch, learned compounding) "
+                         "reported beside the headline")
     ap.add_argument("--sweep-axes", default="voxels,channels,frames", help="axes of --workload sweep")
     return ap.parse_args()
 
